@@ -1,0 +1,184 @@
+"""Pins of the H^2 oracle (generalized H^2-LDL^T, Sec. 3-4) against closed
+forms, the dense oracle and structural invariants.
+
+* TRIDIAG_TEST on integer points: far blocks are exactly zero (rank 0), so the
+  factorization is exact and nu must equal the closed form 2 - 2cos(j pi/(n+1)).
+* MIN_TEST on 1..n: far blocks are exactly rank 1, nested row spans {1, x} need
+  rank 2, fill-ins exist (distance-2 leaves); counts must equal the closed form
+  1/(4 sin^2((2j-1) pi/(4n+2))).
+* Kernel matrices: nu(A~ - mu I) from the generalized LDL equals the dense count
+  of the written-out A~, and of A itself when mu is far from the spectrum
+  relative to ||A - A~||.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dense, h2
+import workloads as W
+
+
+def toeplitz_eigs(n):
+    j = np.arange(1, n + 1)
+    return np.sort(2.0 - 2.0 * np.cos(j * np.pi / (n + 1)))
+
+
+def min_eigs(n):
+    j = np.arange(1, n + 1)
+    return np.sort(1.0 / (4.0 * np.sin((2 * j - 1) * np.pi / (4 * n + 2)) ** 2))
+
+
+def gaps_shifts(ev, step=1):
+    return list(0.5 * (ev[1:] + ev[:-1]))[::step] + [ev[0] - 1.0, ev[-1] + 1.0]
+
+
+@pytest.mark.parametrize("n,leaf", [(64, 8), (100, 16), (37, 5)])
+def test_tridiagonal_exact(n, leaf):
+    h = h2.construct(W.line_points(n), W.TRIDIAG_TEST, (0, 0, 0, 0), leaf, 4, 1.0)
+    assert h.stats["max_rank"] == 0
+    ev = toeplitz_eigs(n)
+    for mu in gaps_shifts(ev, 3):
+        assert h2.h2_inertia(h, mu)[0] == int(np.sum(ev < mu))
+
+
+@pytest.mark.parametrize("n,leaf", [(128, 16), (90, 12)])
+def test_min_matrix_exact(n, leaf):
+    h = h2.construct(W.line_points(n), W.MIN_TEST, (0, 0, 0, 0), leaf, 8, 1.0)
+    assert h.stats["max_rank"] == 2 and h.stats["fill_pairs_leaf"] > 0
+    A = dense.kernel_matrix(W.MIN_TEST, (0, 0, 0, 0), h.X)
+    assert np.linalg.norm(A - h2.dense_approximation(h)) < 1e-12 * np.linalg.norm(A)
+    ev = min_eigs(n)
+    for mu in gaps_shifts(ev, 4):
+        c, mp, info = h2.h2_inertia(h, mu)
+        assert c == int(np.sum(ev < mu))
+
+
+@pytest.fixture(scope="module")
+def lap2d():
+    X = W.uniform_cube(256, 2, 21)
+    h = h2.construct(X, W.LAPLACE_EPS, (1e-3, 0, 0, 0), 32, 16, 1.0)
+    A = dense.kernel_matrix(W.LAPLACE_EPS, (1e-3, 0, 0, 0), h.X)
+    At = h2.dense_approximation(h)
+    return h, A, At
+
+
+def test_structure_invariants(lap2d):
+    h = lap2d[0]
+    st = h.st
+    n = st.n
+    cover = np.zeros((n, n), dtype=np.int64)
+    L = st.L
+    for c, d in zip(*np.nonzero(st.near[L])):
+        a, b = st.rng(L, c)
+        a2, b2 = st.rng(L, d)
+        cover[a:b, a2:b2] += 1
+    for l in range(1, L + 1):
+        for c, d in zip(*np.nonzero(st.far[l])):
+            a, b = st.rng(l, c)
+            a2, b2 = st.rng(l, d)
+            cover[a:b, a2:b2] += 1
+    assert np.all(cover == 1), "every entry lies in exactly one near or far block"
+    for l in range(L + 1):
+        assert np.array_equal(st.near[l], st.near[l].T)
+        assert not np.any(st.near[l] & st.fill[l])
+        if l > 0:
+            assert np.all(st.far[l][st.fill[l]])
+        adj = st.near[l].copy()
+        np.fill_diagonal(adj, False)
+        two = adj | ((adj.astype(int) @ adj.astype(int)) > 0)
+        col = st.colors[l]
+        for c, d in zip(*np.nonzero(two)):
+            if c != d:
+                assert col[c] != col[d], "same-colour clusters are >= 3 apart"
+
+
+def test_bases_orthogonal_and_nested(lap2d):
+    h = lap2d[0]
+    for l in range(h.st.L + 1):
+        for Qc in h.Q[l]:
+            assert np.allclose(Qc.T @ Qc, np.eye(Qc.shape[0]), atol=1e-13)
+        for Ec in h.E[l]:
+            assert np.allclose(Ec.T @ Ec, np.eye(Ec.shape[1]), atol=1e-12)
+
+
+def test_compression_error(lap2d):
+    h, A, At = lap2d
+    assert np.linalg.norm(A - At, 2) <= 1e-8 * np.linalg.norm(A, 2)
+
+
+def test_counts_equal_dense_counts(lap2d):
+    h, A, At = lap2d
+    ev, evt = np.linalg.eigvalsh(A), np.linalg.eigvalsh(At)
+    err = np.linalg.norm(A - At, 2)
+    for mu in gaps_shifts(evt, 17):
+        c, mp, info = h2.h2_inertia(h, mu)
+        assert c == int(np.sum(evt < mu))
+        if np.min(np.abs(ev - mu)) > 2 * err:
+            assert c == int(np.sum(ev < mu))
+
+
+def test_count_monotone_and_gershgorin_ends(lap2d):
+    h = lap2d[0]
+    a, b = h.gershgorin
+    assert h2.h2_inertia(h, a - 1e-6 * h.scale)[0] == 0
+    assert h2.h2_inertia(h, b + 1e-6 * h.scale)[0] == h.st.n
+    prev = 0
+    for mu in np.linspace(950.0, 1100.0, 12):
+        c = h2.h2_inertia(h, mu)[0]
+        assert c >= prev
+        prev = c
+
+
+def test_same_colour_order_commutes(lap2d):
+    """Eliminations inside one colour touch disjoint blocks, so reversing the
+    order within every colour leaves the count unchanged."""
+    h = lap2d[0]
+    st = h.st
+    mus = [960.0, 990.0, 1010.0]
+    base = [h2.h2_inertia(h, mu)[0] for mu in mus]
+    saved = [list(o) for o in st.order]
+    try:
+        for l in range(st.L + 1):
+            st.order[l] = sorted(saved[l], key=lambda c: (st.colors[l][c], -c))
+        assert [h2.h2_inertia(h, mu)[0] for mu in mus] == base
+    finally:
+        st.order = saved
+
+
+def test_permuted_points_same_count():
+    X = W.uniform_cube(200, 2, 31)
+    p = np.argsort(W.uniform(77, 200))
+    h1 = h2.construct(X, W.LAPLACE_EPS, (1e-3, 0, 0, 0), 32, 16, 1.0)
+    h2b = h2.construct(X[p], W.LAPLACE_EPS, (1e-3, 0, 0, 0), 32, 16, 1.0)
+    for mu in (970.0, 1000.0, 1040.0):
+        assert h2.h2_inertia(h1, mu)[0] == h2.h2_inertia(h2b, mu)[0]
+
+
+def test_kth_eigenvalue_3d_within_tolerance():
+    X = W.uniform_cube(320, 3, 41)
+    h = h2.construct(X, W.YUKAWA_EPS, (1e-3, 0, 0, 0), 40, 24, 1.0)
+    A = dense.kernel_matrix(W.YUKAWA_EPS, (1e-3, 0, 0, 0), h.X)
+    ev = np.linalg.eigvalsh(A)
+    err = np.linalg.norm(A - h2.dense_approximation(h), 2)
+    tol = 1e-6
+    ks = [1, 160, 320]
+    mids, lo, hi, evals = h2.kth_eigenvalues(h, ks, tol)
+    for k, lam in zip(ks, mids):
+        assert abs(lam - ev[k - 1]) <= 0.5 * tol + err
+
+
+def test_pivoted_qr_basis_exact_rank():
+    rng = W.gaussian(5, 40 * 3).reshape(40, 3)
+    Y = rng @ W.gaussian(6, 3 * 20).reshape(3, 20)         # rank 3
+    Q, k = h2.pivoted_qr_basis(Y, 1e-10, 10)
+    assert k == 3
+    assert np.linalg.norm(Y - Q[:, :3] @ (Q[:, :3].T @ Y)) < 1e-12 * np.linalg.norm(Y)
+    Q2, k2 = h2.pivoted_qr_basis(Y, 1e-10, 2)                # cap binds
+    assert k2 == 2
+
+
+def test_sketch_matrix_moments():
+    Om = h2.sketch_matrix(4000, 8, 3)
+    assert np.allclose(Om.T @ Om / 4000 * 8, np.eye(8), atol=0.1)
+    assert np.all(np.abs(Om) <= math.sqrt(3.0 / 8))
