@@ -1,0 +1,171 @@
+/*
+ * h2eig.h -- C ABI of the GB300 library for the k-th eigenvalue of a symmetric
+ * kernel matrix compressed as an H^2-matrix, by slicing the spectrum with the
+ * generalized H^2-LDL^T factorization of Apriansyah & Yokota, "Computing the
+ * k-th Eigenvalue of Symmetric H^2-Matrices" (arXiv 2311.08618).
+ *
+ * Problem statement (Sec. 1, Sec. 2): A is n x n real symmetric with entries
+ * A_ij = f(|x_i - x_j|) for points x_i; nu(A - mu I) = #{lambda(A) < mu} is
+ * the number of negative pivots of an LDL^T of the shifted matrix (Sylvester's
+ * law of inertia, Eq. 2); Algorithm 1 bisects on nu to find lambda_k.
+ *
+ * Conventions shared by every entry point:
+ *  - Return H2_OK (0) on success, a negative H2_ERR_* code otherwise; the
+ *    message of the last failure on the calling thread is h2_last_error().
+ *  - No exception crosses this boundary.  Inputs are copied; caller-owned
+ *    outputs are written only on success.
+ *  - Host pointers are plain CPU memory; "device" pointers are CUDA global
+ *    memory on the handle's device.  The library owns all memory it allocates
+ *    and frees it in h2_destroy.
+ *  - A handle is used by one host thread at a time (one handle per stream).
+ *  - Every computation runs in the library's CUDA kernels; there is no CPU
+ *    fallback.  Without a usable CUDA device, h2_build fails with H2_ERR_CUDA.
+ */
+#ifndef H2EIG_H
+#define H2EIG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define H2_OK               0
+#define H2_ERR_INVALID_ARG (-1)  /* a null pointer, n < 1, k out of 1..n, ... */
+#define H2_ERR_OOM         (-2)  /* device allocation failed                  */
+#define H2_ERR_NUMERICAL   (-3)  /* NaN/Inf met in the factorization           */
+#define H2_ERR_TIMEOUT     (-4)  /* a bounded device wait ran out              */
+#define H2_ERR_INTERVAL    (-5)  /* nu(a) != 0 or nu(b) != n at the start      */
+#define H2_ERR_CUDA        (-6)  /* a CUDA runtime call failed                 */
+
+/* ---- kernels f(r) (Sec. 5.1 and the synthetic workloads) ----------------- */
+typedef enum {
+    H2_K_LAPLACE_EPS    = 0,  /* 1/(r + p0)              (Sec. 5.1, p0 = 1e-3) */
+    H2_K_YUKAWA_EPS     = 1,  /* exp(-r)/(r + p0)                              */
+    H2_K_GAUSS_PLUS_INV = 2,  /* exp(-r^2/2) + p0/(r + p1)                     */
+    H2_K_TRIDIAG_TEST   = 3,  /* 2 at r = 0, -1 at r = 1, else 0 (1D integers) */
+    H2_K_MIN_TEST       = 4   /* min(x_i, x_j) of the first coordinates        */
+} h2_kernel_kind;
+
+typedef struct {
+    int kind;        /* an h2_kernel_kind */
+    double p[4];     /* its parameters, unused entries ignored */
+} h2_kernel;
+
+/* ---- options ------------------------------------------------------------ */
+#define H2_ADM_BOX    0  /* max(diam c, diam d) <= eta * dist(box c, box d) */
+#define H2_ADM_CENTER 1  /* (diam c + diam d)/2 <= eta * |center c - center d| */
+
+#define H2_PREC_FP64  0  /* every step in FP64 */
+
+typedef struct {
+    int precision;       /* H2_PREC_FP64 */
+    int admissibility;   /* H2_ADM_BOX (default) or H2_ADM_CENTER */
+    double eps_h2;       /* truncation tolerance relative to ||A||_inf (Sec. 3.1,
+                            eps_H2; default 1e-10 = 1e-2 * 1e-8, Sec. 5) */
+    int fill_cap;        /* max skeleton columns per cluster after fill-in
+                            recompression (Sec. 3.4); 0 = 2 * rank */
+    int sketch_cols;     /* columns of the random sketch of A_{l;c,+}; 0 = rank + 16 */
+    uint64_t seed;       /* SplitMix64 state for the sketch matrix */
+    int max_lanes;       /* shifts factorized concurrently; 0 = 64 */
+    void* stream;        /* cudaStream_t for all work of the handle; NULL = a
+                            stream created by the library */
+} h2_options;
+
+/* Fills *opt with the defaults above.  Never fails. */
+void h2_default_options(h2_options* opt);
+
+/* ---- handle lifecycle ---------------------------------------------------- */
+typedef struct h2_matrix* h2_handle;
+
+/*
+ * h2_build -- construct the H^2 matrix of A_ij = f(|x_i - x_j|) (Sec. 3.1,
+ * Eqs. shared-bases, transfer-matrices, dense_skeleton, lr_skeleton) and keep
+ * it resident and factor-ready on the current CUDA device.
+ *   points : host, n x d row-major FP64, copied.
+ *   n >= 1, 1 <= d <= 3, leaf >= 2 (maximum points per leaf cluster),
+ *   rank   : cap on the skeleton rank of each shared basis (>= 0),
+ *   eta > 0: strong-admissibility parameter.
+ *   opt    : NULL for defaults.
+ *   *out   : receives the handle on success, untouched on failure.
+ * Errors: H2_ERR_INVALID_ARG, H2_ERR_OOM, H2_ERR_CUDA.
+ */
+int h2_build(const double* points, int64_t n, int d, h2_kernel kernel, int leaf,
+             int rank, double eta, const h2_options* opt, h2_handle* out);
+
+/* Frees every resource of h.  NULL is a no-op. */
+void h2_destroy(h2_handle h);
+
+/* Message of the last failure of an h2_* call on this thread ("" if none). */
+const char* h2_last_error(void);
+
+/* ---- inertia (Sec. 4, Eq. 2 with Eq. h2-generalized-ldl) ------------------ */
+/*
+ * h2_inertia -- counts[i] = nu(A~ - shifts[i] I) = #{j : D_jj < 0} of the
+ * generalized H^2-LDL^T of the shifted matrix (strict: a zero pivot is not
+ * negative).  min_abs_pivot[i] (nullable) = the smallest |eigenvalue| of a
+ * 1x1 or 2x2 block of D, a guard for shifts close to an eigenvalue.
+ *   shifts        : host, ns FP64.
+ *   counts        : host, caller-owned, ns int64.
+ *   min_abs_pivot : host, caller-owned, ns FP64, or NULL.
+ * Shifts are processed in batches of max_lanes.  Blocks until done.
+ */
+int h2_inertia(h2_handle h, const double* shifts, int64_t ns, int64_t* counts,
+               double* min_abs_pivot);
+
+/*
+ * h2_inertia_device -- as h2_inertia with DEVICE pointers; enqueued on the
+ * handle's stream and returns without waiting (ns <= max_lanes).
+ */
+int h2_inertia_device(h2_handle h, const double* d_shifts, int64_t ns, int64_t* d_counts,
+                      double* d_min_abs_pivot);
+
+/* ---- k-th eigenvalues (Algorithm 1 with the inertia reuse of Sec. 4.2) ---- */
+/*
+ * h2_kth_eig -- out[i] = lambda~_{k[i]} of A~, the midpoint of a final
+ * interval of width < tol found by bisection/multisection from the Gershgorin
+ * interval (|lambda_k - lambda~_k| < tol/2, Eq. error-bound).  Every evaluated
+ * (mu, nu) narrows every k (Sec. 4.2); each round spreads max_lanes shifts
+ * over the distinct active intervals.  The intervals stay on the device.
+ *   k         : host, nk int64, 1-based, each in 1..n.
+ *   tol > 0   : absolute interval width.
+ *   out       : host, caller-owned, nk FP64.
+ *   err_bound : host, caller-owned, nk FP64 (half the final width), or NULL.
+ * Errors: H2_ERR_INVALID_ARG, H2_ERR_INTERVAL, H2_ERR_NUMERICAL, H2_ERR_CUDA.
+ */
+int h2_kth_eig(h2_handle h, const int64_t* k, int64_t nk, double tol, double* out,
+               double* err_bound);
+
+/* ---- introspection -------------------------------------------------------- */
+typedef struct {
+    int64_t n;
+    int levels;              /* L + 1 (root level 0 .. leaf level L) */
+    int leaves;
+    int max_rank;            /* largest build rank of any shared basis */
+    int64_t near_pairs;      /* ordered leaf pairs stored dense */
+    int64_t fill_pairs;      /* ordered leaf pairs receiving fill-ins */
+    double norm_inf;         /* ||A||_inf (max absolute row sum) */
+    double gershgorin_lo;    /* min_i (A_ii - R_i) */
+    double gershgorin_hi;    /* max_i (A_ii + R_i) */
+    double trunc_tol;        /* eps_h2 * ||A||_inf */
+    int64_t workspace_bytes; /* per-batch factorization workspace */
+    int lanes;               /* shifts per batch */
+} h2_stats;
+
+int h2_info(h2_handle h, h2_stats* out);
+
+/* tree order: perm[i] = index (0-based, in the input) of the i-th point in
+ * tree order.  perm: host, caller-owned, n int64. */
+int h2_tree_perm(h2_handle h, int64_t* perm);
+
+/* build ranks of the shared bases of level `level` (0 = root .. L = leaves);
+ * ranks: host, caller-owned, 2^level ints. */
+int h2_level_ranks(h2_handle h, int level, int* ranks);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* H2EIG_H */

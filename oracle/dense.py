@@ -58,8 +58,14 @@ def kernel_matrix(kind: int, p, X: np.ndarray) -> np.ndarray:
     return kernel_block(kind, p, X, X)
 
 
-def bk_ldl(A: np.ndarray):
+def bk_ldl(A: np.ndarray, zero_pivot: float = 0.0):
     """Bunch-Kaufman LDL^T of a symmetric matrix (Bunch & Kaufman 1977).
+
+    ``zero_pivot``: value stored for a 1x1 pivot that is exactly zero (its
+    column is then zero too, so nothing is eliminated).  The dense count keeps
+    0; the generalized H^2 factorization passes eps * ||A||_inf so that its
+    block elimination S^{xR} D^{-1} stays finite when a cluster's redundant
+    block is exactly singular (a perturbation of size eps ||A||).
 
     Returns (perm, L, blocks) with A[perm][:, perm] = L D L^T, L unit lower
     triangular and D block diagonal; ``blocks`` lists (start, size, E) for every
@@ -111,6 +117,9 @@ def bk_ldl(A: np.ndarray):
                 size = 2
         if size == 1:
             d = S[k, k]
+            if d == 0.0 and zero_pivot != 0.0:
+                d = zero_pivot
+                S[k, k] = d
             blocks.append((k, 1, np.array([[d]])))
             if d != 0.0 and k + 1 < n:
                 l = S[k + 1:, k] / d
@@ -208,6 +217,12 @@ def jacobi_eigenvalues(A: np.ndarray, sweeps: int = 60, tol: float = 1e-15) -> n
                 S[:, p] = c * cp - s * cq
                 S[:, q] = s * cp + c * cq
     return np.sort(np.diag(S))
+
+
+def eigenvalues(A: np.ndarray) -> np.ndarray:
+    """All eigenvalues of the symmetric A by LAPACK (numpy eigvalsh), the
+    dense comparison solver of Sec. 5 (dsyev); pinned against Jacobi in tests."""
+    return np.linalg.eigvalsh(A)
 
 
 def gershgorin(A: np.ndarray):

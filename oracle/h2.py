@@ -40,7 +40,10 @@ Readings taken where the paper is silent (each also listed in the design notes):
   ``fill_cap`` total skeleton columns) gives an orthogonal rotation of p's
   redundant coordinates; its leading t columns join the skeleton, and the
   remaining redundant rows of the fill-in blocks (norm <= tol) are dropped.
-* Local pivoting: Bunch-Kaufman within each cluster's redundant block.
+* Local pivoting: Bunch-Kaufman within each cluster's redundant block.  A 1x1
+  pivot that is exactly zero (the cluster's redundant block is exactly
+  singular while it still couples to other blocks) is replaced by
+  eps * ||A||_inf, a perturbation of that size; min |pivot| then flags the shift.
 * Inertia: nu = total number of negative pivots over all levels (Sec. 4,
   Sylvester); a 2x2 pivot counts by det and trace.
 """
@@ -363,8 +366,8 @@ class _Level:
         return np.arange(self.rk[a]) if self.elim[a] else np.arange(self.dim[a])
 
 
-def _bk_solve_parts(Braw):
-    perm, Lf, blocks = dense.bk_ldl(Braw)
+def _bk_solve_parts(Braw, zero_pivot):
+    perm, Lf, blocks = dense.bk_ldl(Braw, zero_pivot)
     Dm = np.zeros_like(Braw)
     for s0, sz, Eb in blocks:
         Dm[s0:s0 + sz, s0:s0 + sz] = Eb
@@ -401,7 +404,7 @@ def _recompress(lv: _Level, st: Structure, l: int, p: int, tol: float, cap: int,
     info["max_skel"] = max(info["max_skel"], lv.rk[p])
 
 
-def _eliminate(lv: _Level, st: Structure, l: int, p: int, info):
+def _eliminate(lv: _Level, st: Structure, l: int, p: int, info, zero_pivot):
     """Eqs. blr2-diag-ldl, -elimination, -schur for cluster p: LDL^T of
     S_pp^RR, L^{xR} = S^{xR} L^{-T} D^{-1} for every live block x coupled to
     p's redundant part, and S_xy -= L^{xR} D L^{yR T} on all such pairs."""
@@ -410,7 +413,7 @@ def _eliminate(lv: _Level, st: Structure, l: int, p: int, info):
     if len(Rs) == 0:
         return
     BRR = lv.get(p, p)[np.ix_(Rs, Rs)]
-    perm, Lf, Dm, blocks = _bk_solve_parts(BRR)
+    perm, Lf, Dm, blocks = _bk_solve_parts(BRR, zero_pivot)
     neg, mn = dense.inertia_from_blocks(blocks)
     info["neg"] += neg
     info["minpiv"] = min(info["minpiv"], mn)
@@ -505,7 +508,7 @@ def h2_inertia(h: H2Matrix, sigma: float):
     for l in range(L, -1, -1):
         for p in st.order[l]:
             _recompress(lv, st, l, p, h.tol, h.fill_cap, info)
-            _eliminate(lv, st, l, p, info)
+            _eliminate(lv, st, l, p, info, np.finfo(np.float64).eps * h.scale)
         if l > 0:
             lv = _merge(h, st, l, lv)
     return info["neg"], info["minpiv"], info

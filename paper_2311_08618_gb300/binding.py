@@ -1,0 +1,164 @@
+"""ctypes binding of include/h2eig.h: argument marshalling only.
+
+Every entry point keeps its C name on the raw library object ``lib()``; the
+``H2Matrix`` class wraps a handle.  Device-pointer entry points accept any
+object with ``data_ptr()`` (a torch CUDA tensor) or a raw integer address.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+H2_K_LAPLACE_EPS, H2_K_YUKAWA_EPS, H2_K_GAUSS_PLUS_INV, H2_K_TRIDIAG_TEST, H2_K_MIN_TEST = 0, 1, 2, 3, 4
+H2_ADM_BOX, H2_ADM_CENTER = 0, 1
+
+EXPORTED_SYMBOLS = ["h2_default_options", "h2_build", "h2_destroy", "h2_last_error", "h2_inertia",
+                    "h2_inertia_device", "h2_kth_eig", "h2_info", "h2_tree_perm", "h2_level_ranks"]
+
+
+class Kernel(C.Structure):
+    _fields_ = [("kind", C.c_int), ("p", C.c_double * 4)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("admissibility", C.c_int), ("eps_h2", C.c_double),
+                ("fill_cap", C.c_int), ("sketch_cols", C.c_int), ("seed", C.c_uint64),
+                ("max_lanes", C.c_int), ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("levels", C.c_int), ("leaves", C.c_int), ("max_rank", C.c_int),
+                ("near_pairs", C.c_int64), ("fill_pairs", C.c_int64), ("norm_inf", C.c_double),
+                ("gershgorin_lo", C.c_double), ("gershgorin_hi", C.c_double), ("trunc_tol", C.c_double),
+                ("workspace_bytes", C.c_int64), ("lanes", C.c_int)]
+
+
+class H2Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("h2eig error %d: %s" % (code, msg))
+        self.code = code
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return os.path.join(HERE, "libh2eig.so")
+
+
+def lib():
+    """The loaded libh2eig.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise ImportError("libh2eig.so is not built: run `python -m paper_2311_08618_gb300.build`")
+        L = C.CDLL(path)
+        P = C.c_void_p
+        L.h2_default_options.argtypes = [C.POINTER(Options)]
+        L.h2_default_options.restype = None
+        L.h2_build.argtypes = [P, C.c_int64, C.c_int, Kernel, C.c_int, C.c_int, C.c_double,
+                               C.POINTER(Options), C.POINTER(P)]
+        L.h2_destroy.argtypes = [P]
+        L.h2_destroy.restype = None
+        L.h2_last_error.restype = C.c_char_p
+        L.h2_inertia.argtypes = [P, P, C.c_int64, P, P]
+        L.h2_inertia_device.argtypes = [P, P, C.c_int64, P, P]
+        L.h2_kth_eig.argtypes = [P, P, C.c_int64, C.c_double, P, P]
+        L.h2_info.argtypes = [P, C.POINTER(Stats)]
+        L.h2_tree_perm.argtypes = [P, P]
+        L.h2_level_ranks.argtypes = [P, C.c_int, P]
+        for f in ("h2_build", "h2_inertia", "h2_inertia_device", "h2_kth_eig", "h2_info",
+                  "h2_tree_perm", "h2_level_ranks"):
+            getattr(L, f).restype = C.c_int
+        _LIB = L
+    return _LIB
+
+
+def _check(rc):
+    if rc != 0:
+        raise H2Error(rc, lib().h2_last_error().decode())
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(int(x))
+
+
+def default_options() -> Options:
+    o = Options()
+    lib().h2_default_options(C.byref(o))
+    return o
+
+
+class H2Matrix:
+    """A resident, factor-ready H^2 matrix (h2_build ... h2_destroy)."""
+
+    def __init__(self, points, kernel: int, kparams=(1e-3, 0.0, 0.0, 0.0), leaf: int = 64,
+                 rank: int = 16, eta: float = 1.0, **opts):
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        if pts.ndim == 1:
+            pts = pts.reshape(-1, 1)
+        o = default_options()
+        for k, v in opts.items():
+            if k == "stream" and v is not None and not isinstance(v, int):
+                v = v.cuda_stream
+            setattr(o, k, v)
+        kr = Kernel(kernel, (C.c_double * 4)(*[float(v) for v in (list(kparams) + [0, 0, 0, 0])[:4]]))
+        h = C.c_void_p()
+        _check(lib().h2_build(pts.ctypes.data_as(C.c_void_p), pts.shape[0], pts.shape[1], kr, leaf, rank,
+                              eta, C.byref(o), C.byref(h)))
+        self._h = h
+        self.n = pts.shape[0]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().h2_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def h2_inertia(self, shifts):
+        s = np.ascontiguousarray(shifts, dtype=np.float64).ravel()
+        counts = np.zeros(s.size, dtype=np.int64)
+        mp = np.zeros(s.size, dtype=np.float64)
+        _check(lib().h2_inertia(self._h, s.ctypes.data_as(C.c_void_p), s.size,
+                                counts.ctypes.data_as(C.c_void_p), mp.ctypes.data_as(C.c_void_p)))
+        return counts, mp
+
+    def h2_inertia_device(self, d_shifts, ns, d_counts, d_minpiv=None):
+        _check(lib().h2_inertia_device(self._h, _ptr(d_shifts), int(ns), _ptr(d_counts), _ptr(d_minpiv)))
+
+    def h2_kth_eig(self, ks, tol):
+        k = np.ascontiguousarray(ks, dtype=np.int64).ravel()
+        out = np.zeros(k.size)
+        eb = np.zeros(k.size)
+        _check(lib().h2_kth_eig(self._h, k.ctypes.data_as(C.c_void_p), k.size, float(tol),
+                                out.ctypes.data_as(C.c_void_p), eb.ctypes.data_as(C.c_void_p)))
+        return out, eb
+
+    def h2_info(self) -> dict:
+        s = Stats()
+        _check(lib().h2_info(self._h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def h2_tree_perm(self):
+        p = np.zeros(self.n, dtype=np.int64)
+        _check(lib().h2_tree_perm(self._h, p.ctypes.data_as(C.c_void_p)))
+        return p
+
+    def h2_level_ranks(self, level):
+        r = np.zeros(1 << level, dtype=np.int32)
+        _check(lib().h2_level_ranks(self._h, int(level), r.ctypes.data_as(C.c_void_p)))
+        return r

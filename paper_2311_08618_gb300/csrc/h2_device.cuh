@@ -1,0 +1,351 @@
+// Device helpers shared by the construction and factorization kernels:
+// kernel entries, the sketch generator and CTA-cooperative dense routines
+// (Householder QR with column pivoting, Bunch-Kaufman LDL^T) in FP64.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace h2dev {
+
+// --------------------------------------------------------------- kernels --
+struct KernelSpec {
+    int kind;
+    double p0, p1, p2, p3;
+};
+
+// A_ij = f(|x_i - x_j|) for the kernels of Sec. 5 (see h2_kernel_kind).
+__device__ __forceinline__ double kernel_entry(const KernelSpec& k, const double* xi,
+                                               const double* xj) {
+    double dx = xi[0] - xj[0], dy = xi[1] - xj[1], dz = xi[2] - xj[2];
+    double r = sqrt(dx * dx + dy * dy + dz * dz);
+    switch (k.kind) {
+        case 0: return 1.0 / (r + k.p0);
+        case 1: return exp(-r) / (r + k.p0);
+        case 2: return exp(-0.5 * r * r) + k.p0 / (r + k.p1);
+        case 3: return r < 0.5 ? 2.0 : (fabs(r - 1.0) < 0.5 ? -1.0 : 0.0);
+        default: return fmin(xi[0], xj[0]);
+    }
+}
+
+// SplitMix64 (Vigna; Steele, Lea & Flood 2014): output number `idx` (0-based)
+// of the generator started at state `seed`.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t idx) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (idx + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Sketch entry Omega[i][c] = (2u - 1) * scale, u = top 53 bits * 2^-53.
+__device__ __forceinline__ double sketch_entry(uint64_t seed, int64_t i, int c, int s,
+                                               double scale) {
+    uint64_t z = splitmix64_at(seed, (uint64_t)i * (uint64_t)s + (uint64_t)c);
+    double u = (double)(z >> 11) * 0x1.0p-53;
+    return (2.0 * u - 1.0) * scale;
+}
+
+// ------------------------------------------------------- block reductions --
+template <int NT>
+__device__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < NT / 32 ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[0] = v;
+    }
+    __syncthreads();
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// argmax with the first index on ties; returns index, writes value
+template <int NT>
+__device__ int block_argmax(double v, int idx, double* redv, int* redi, double* outv) {
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) { redv[w] = v; redi[w] = idx; }
+    __syncthreads();
+    if (w == 0) {
+        v = lane < NT / 32 ? redv[lane] : -1.0;
+        idx = lane < NT / 32 ? redi[lane] : 0x7fffffff;
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, v, o);
+            int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+            if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+        }
+        if (lane == 0) { redv[0] = v; redi[0] = idx; }
+    }
+    __syncthreads();
+    int r = redi[0];
+    *outv = redv[0];
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------- pivoted Householder QR --
+// Householder QR with column pivoting of Y (m x s, row-major, leading
+// dimension ldy), in place, stopped when the Frobenius norm of the
+// not-yet-pivoted remainder Y[k:, k:] is <= tol, or after `cap` steps.
+// Reflector k is stored in V (row-major m x ldv, column k, rows k..m-1,
+// unit 2-norm; a zero vector means H_k = I).  colnorm: scratch of s doubles.
+// Returns k (the rank).  All threads of the CTA call it.
+template <int NT>
+__device__ int cta_pivqr(double* Y, int ldy, int m, int s, double tol, int cap, double* V,
+                         int ldv, double* colnorm, double* red, int* redi, int* bad = nullptr) {
+    int kmax = min(min(m, s), cap);
+    int k = 0;
+    for (; k < kmax; ++k) {
+        // trailing column norms (exact recomputation, no downdating)
+        for (int j = k + threadIdx.x; j < s; j += NT) {
+            double a = 0.0;
+            for (int i = k; i < m; ++i) {
+                double y = Y[(size_t)i * ldy + j];
+                a += y * y;
+            }
+            colnorm[j] = a;
+        }
+        __syncthreads();
+        double part = 0.0, best = -1.0;
+        int bi = 0x7fffffff;
+        for (int j = k + threadIdx.x; j < s; j += NT) {
+            part += colnorm[j];
+            if (colnorm[j] > best) { best = colnorm[j]; bi = j; }
+        }
+        double total = block_sum<NT>(part, red);
+        if (!(total == total)) {          // NaN input: stop, report, touch nothing
+            if (bad && threadIdx.x == 0) *bad = 1;
+            break;
+        }
+        if (sqrt(total) <= tol) break;
+        double bv;
+        int jp = block_argmax<NT>(best, bi, red, redi, &bv);
+        if (jp < k || jp >= s) jp = k;
+        if (jp != k)
+            for (int i = threadIdx.x; i < m; i += NT) {
+                double t = Y[(size_t)i * ldy + k];
+                Y[(size_t)i * ldy + k] = Y[(size_t)i * ldy + jp];
+                Y[(size_t)i * ldy + jp] = t;
+            }
+        __syncthreads();
+        // reflector from x = Y[k:, k]
+        double nx2 = 0.0;
+        for (int i = k + threadIdx.x; i < m; i += NT) {
+            double x = Y[(size_t)i * ldy + k];
+            nx2 += x * x;
+        }
+        nx2 = block_sum<NT>(nx2, red);
+        double nx = sqrt(nx2);
+        double x0 = Y[(size_t)k * ldy + k];
+        double alpha = x0 >= 0.0 ? -nx : nx;
+        // |v|^2 = |x|^2 - 2 alpha x0 + alpha^2 = 2 nx^2 - 2 alpha x0
+        double v0 = x0 - alpha;
+        double nv2 = 0.0;
+        for (int i = k + threadIdx.x; i < m; i += NT) {
+            double x = (i == k) ? v0 : Y[(size_t)i * ldy + k];
+            nv2 += x * x;
+        }
+        nv2 = block_sum<NT>(nv2, red);
+        double nv = sqrt(nv2);
+        for (int i = threadIdx.x; i < m; i += NT) {
+            double x = 0.0;
+            if (i >= k && nv > 0.0) x = ((i == k) ? v0 : Y[(size_t)i * ldy + k]) / nv;
+            V[(size_t)i * ldv + k] = x;
+        }
+        __syncthreads();
+        if (nv > 0.0) {
+            // Y[k:, j] -= 2 v (v . Y[k:, j]) for j >= k
+            for (int j = k + threadIdx.x; j < s; j += NT) {
+                double w = 0.0;
+                for (int i = k; i < m; ++i) w += V[(size_t)i * ldv + k] * Y[(size_t)i * ldy + j];
+                w *= 2.0;
+                for (int i = k; i < m; ++i) Y[(size_t)i * ldy + j] -= w * V[(size_t)i * ldv + k];
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    return k;
+}
+
+// Q = H_0 H_1 ... H_{k-1} (m x m, row-major, leading dimension ldq) from the
+// reflectors stored by cta_pivqr.
+template <int NT>
+__device__ void cta_form_q(double* Q, int ldq, int m, const double* V, int ldv, int k) {
+    for (int e = threadIdx.x; e < m * m; e += NT) {
+        int i = e / m, j = e % m;
+        Q[(size_t)i * ldq + j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int r = k - 1; r >= 0; --r) {
+        // Q[r:, :] -= 2 v (v^T Q[r:, :])
+        for (int j = threadIdx.x; j < m; j += NT) {
+            double w = 0.0;
+            for (int i = r; i < m; ++i) w += V[(size_t)i * ldv + r] * Q[(size_t)i * ldq + j];
+            w *= 2.0;
+            if (w != 0.0)
+                for (int i = r; i < m; ++i) Q[(size_t)i * ldq + j] -= w * V[(size_t)i * ldv + r];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------ Bunch-Kaufman LDL --
+// In-place Bunch-Kaufman LDL^T (partial pivoting, alpha = (1 + sqrt 17)/8) of
+// the full symmetric n x n matrix S (row-major, leading dimension lds).  On
+// return the strict lower triangle holds L (except the (k+1, k) entry of a
+// 2x2 pivot, which is D's off-diagonal), the diagonal holds D, perm[j] is the
+// original index of position j, and piv[j] = 1 (1x1), 2 (first of a 2x2),
+// 0 (second of a 2x2).  Accumulates #negative eigenvalues of D into *neg and
+// the smallest |eigenvalue| of a D block into *minpiv (thread 0's values).
+template <int NT>
+__device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, double* red,
+                           int* redi, int* neg, double* minpiv, int* bad, double zero_pivot) {
+    const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+    for (int i = threadIdx.x; i < n; i += NT) perm[i] = i;
+    __syncthreads();
+    int k = 0;
+    int nneg = 0;
+    double mp = 1.0 / 0.0;
+    while (k < n) {
+        double akk = fabs(S[(size_t)k * lds + k]);
+        // lam = max_{i>k} |S_ik|, r = first index attaining it
+        double best = -1.0;
+        int bi = 0x7fffffff;
+        for (int i = k + 1 + threadIdx.x; i < n; i += NT) {
+            double v = fabs(S[(size_t)i * lds + k]);
+            if (v > best) { best = v; bi = i; }
+        }
+        double lam;
+        int r = block_argmax<NT>(best, bi, red, redi, &lam);
+        if (k + 1 >= n) { lam = 0.0; r = k; }
+        else if (r <= k || r >= n) r = k + 1;
+        int size = 1;
+        int swap_a = -1, swap_b = -1;
+        if (!(akk == akk) || !(lam == lam)) {
+            if (threadIdx.x == 0) *bad = 1;   // NaN: finish with 1x1 steps, flagged
+        } else if (!(lam == 0.0 || akk >= alpha * lam)) {
+            double b2 = -1.0;
+            int bj = 0x7fffffff;
+            for (int j = k + threadIdx.x; j < n; j += NT) {
+                if (j == r) continue;
+                double v = fabs(S[(size_t)j * lds + r]);
+                if (v > b2) { b2 = v; bj = j; }
+            }
+            double sig;
+            block_argmax<NT>(b2, bj, red, redi, &sig);
+            if (sig < 0.0) sig = 0.0;
+            if (akk * sig >= alpha * lam * lam) {
+                // 1x1 at k
+            } else if (fabs(S[(size_t)r * lds + r]) >= alpha * sig) {
+                swap_a = k; swap_b = r;
+            } else {
+                swap_a = k + 1; swap_b = r;
+                size = 2;
+            }
+        }
+        if (swap_a >= 0 && swap_a != swap_b) {
+            // swap rows then columns swap_a <-> swap_b (all of them)
+            for (int j = threadIdx.x; j < n; j += NT) {
+                double t = S[(size_t)swap_a * lds + j];
+                S[(size_t)swap_a * lds + j] = S[(size_t)swap_b * lds + j];
+                S[(size_t)swap_b * lds + j] = t;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += NT) {
+                double t = S[(size_t)i * lds + swap_a];
+                S[(size_t)i * lds + swap_a] = S[(size_t)i * lds + swap_b];
+                S[(size_t)i * lds + swap_b] = t;
+            }
+            if (threadIdx.x == 0) {
+                int t = perm[swap_a];
+                perm[swap_a] = perm[swap_b];
+                perm[swap_b] = t;
+            }
+            __syncthreads();
+        }
+        if (size == 1) {
+            double d = S[(size_t)k * lds + k];
+            if (d == 0.0 && zero_pivot != 0.0) {
+                // exactly zero pivot with a zero column: stored as zero_pivot
+                __syncthreads();
+                d = zero_pivot;
+                if (threadIdx.x == 0) S[(size_t)k * lds + k] = d;
+            }
+            if (threadIdx.x == 0) {
+                piv[k] = 1;
+                if (d < 0.0) nneg += 1;
+                mp = fmin(mp, fabs(d));
+                if (d != d) *bad = 1;
+            }
+            if (d != 0.0 && k + 1 < n) {
+                // l = S[k+1:, k] / d ; S[k+1:, k+1:] -= l * S[k+1:, k]^T
+                int t = n - k - 1;
+                for (int e = threadIdx.x; e < t * t; e += NT) {
+                    int i = k + 1 + e / t, j = k + 1 + e % t;
+                    S[(size_t)i * lds + j] -= (S[(size_t)i * lds + k] / d) * S[(size_t)j * lds + k];
+                }
+                __syncthreads();
+                for (int i = k + 1 + threadIdx.x; i < n; i += NT) S[(size_t)i * lds + k] /= d;
+            }
+            __syncthreads();
+            k += 1;
+        } else {
+            double a = S[(size_t)k * lds + k], b = S[(size_t)(k + 1) * lds + k],
+                   c = S[(size_t)(k + 1) * lds + k + 1];
+            double det = a * c - b * b;
+            if (threadIdx.x == 0) {
+                piv[k] = 2;
+                piv[k + 1] = 0;
+                double tr = a + c;
+                nneg += det < 0.0 ? 1 : (tr < 0.0 ? 2 : 0);
+                double disc = sqrt(fmax(0.0, 0.25 * (a - c) * (a - c) + b * b));
+                double e0 = 0.5 * tr - disc, e1 = 0.5 * tr + disc;
+                mp = fmin(mp, fmin(fabs(e0), fabs(e1)));
+                if (det != det) *bad = 1;
+            }
+            if (k + 2 < n) {
+                // Lc = C E^{-1}; S[k+2:, k+2:] -= Lc C^T ; store Lc in S[k+2:, k:k+2]
+                double i00 = c / det, i01 = -b / det, i11 = a / det;
+                int t = n - k - 2;
+                for (int e = threadIdx.x; e < t * t; e += NT) {
+                    int i = k + 2 + e / t, j = k + 2 + e % t;
+                    double ci0 = S[(size_t)i * lds + k], ci1 = S[(size_t)i * lds + k + 1];
+                    double l0 = ci0 * i00 + ci1 * i01, l1 = ci0 * i01 + ci1 * i11;
+                    S[(size_t)i * lds + j] -= l0 * S[(size_t)j * lds + k] + l1 * S[(size_t)j * lds + k + 1];
+                }
+                __syncthreads();
+                for (int i = k + 2 + threadIdx.x; i < n; i += NT) {
+                    double ci0 = S[(size_t)i * lds + k], ci1 = S[(size_t)i * lds + k + 1];
+                    S[(size_t)i * lds + k] = ci0 * i00 + ci1 * i01;
+                    S[(size_t)i * lds + k + 1] = ci0 * i01 + ci1 * i11;
+                }
+            }
+            __syncthreads();
+            k += 2;
+        }
+    }
+    if (threadIdx.x == 0) {
+        *neg += nneg;
+        *minpiv = fmin(*minpiv, mp);
+    }
+    __syncthreads();
+}
+
+// L(j, i) of the unit lower factor stored by cta_bk_ldl (i < j).
+__device__ __forceinline__ double bk_L(const double* S, int lds, const int* piv, int j, int i) {
+    if (piv[i] == 2 && j == i + 1) return 0.0;
+    return S[(size_t)j * lds + i];
+}
+
+}  // namespace h2dev

@@ -1,0 +1,953 @@
+// Per-shift generalized H^2-LDL^T factorization and inertia count on the device
+// (Sec. 3.2-3.4 and Sec. 4), and the multi-interval bisection driver
+// (Algorithm 1 with the inertia reuse of Sec. 4.2).
+//
+// One batch factorizes `lanes` shifted matrices A~ - sigma_b I at once.  Per
+// level (leaves first) and per colour of the level's distance-2 colouring:
+//   k_factor : one CTA per (cluster p of the colour, lane): fill-in
+//              recompression of row p (pivoted QR of the fill-in blocks'
+//              redundant rows, rotation of p's redundant coordinates), the
+//              Bunch-Kaufman LDL^T of S_pp^RR with its negative-pivot count,
+//              and W_a = S_ap^{.R} P L^{-T}, Y_a = W_a D^{-1} for every block
+//              coupled to p's redundant part (Eqs. blr2-diag-ldl, -elimination);
+//   k_schur  : S_ab -= W_a Y_b^T on every pair of those blocks (Eq. blr2-diag-schur),
+//              tiled 32 x 32 per CTA;
+// then k_merge gathers the children's skeleton blocks into the parent level
+// and applies the transfer bases (Sec. 3.3).  The whole sequence is captured
+// once into a CUDA graph and replayed per batch.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "h2_device.cuh"
+#include "h2_internal.h"
+
+using namespace h2dev;
+
+namespace h2 {
+
+#define CK(x)                                                                       \
+    do {                                                                            \
+        cudaError_t e_ = (x);                                                       \
+        if (e_ != cudaSuccess) {                                                    \
+            set_error(std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #x); \
+            return e_ == cudaErrorMemoryAllocation ? H2_ERR_OOM : H2_ERR_CUDA;      \
+        }                                                                           \
+    } while (0)
+
+template <typename T>
+static int dalloc(T** p, size_t count) {
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return H2_ERR_OOM;
+    }
+    return H2_OK;
+}
+
+template <typename T>
+static int upload(T** p, const std::vector<T>& v) {
+    int rc = dalloc(p, v.size());
+    if (rc) return rc;
+    if (!v.empty()) CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return H2_OK;
+}
+
+constexpr int NT = 256;
+constexpr int TS = 32;   // Schur tile
+
+// scratch layout of one elimination (offsets in doubles)
+struct ScratchLayout {
+    size_t z, colnorm, vr, vq, tmp, f, iperm, hdr, w, y, total;
+};
+
+static ScratchLayout scratch_layout(int D, int nfill_max, int ntarg_max) {
+    ScratchLayout s{};
+    size_t zcols = (size_t)std::max(nfill_max, 1) * D;
+    size_t o = 0;
+    s.z = o; o += (size_t)D * zcols;
+    s.colnorm = o; o += zcols;
+    s.vr = o; o += (size_t)D * D;
+    s.vq = o; o += (size_t)D * D;
+    s.tmp = o; o += (size_t)D * D;
+    s.f = o; o += (size_t)D * D;
+    s.iperm = o; o += (size_t)D;              // 2*D ints
+    s.hdr = o; o += 8 + (size_t)(ntarg_max + 1) / 2 + 1;   // ints
+    s.w = o; o += (size_t)ntarg_max * D * D;
+    s.y = o; o += (size_t)ntarg_max * D * D;
+    s.total = (o + 3) & ~(size_t)3;
+    return s;
+}
+
+struct FactorArgs {
+    double* slots;
+    int D, lanes;
+    int* dim;
+    int* rk;
+    const int* color;
+    int cur_color;
+    const int* cl;
+    const int* targ;
+    const int* targ_slot;
+    const int* targ_trans;
+    const int* ntarg;
+    int ntarg_max;
+    const int* rowblk;
+    const int* rowblk_other;
+    const int* rowblk_trans;
+    const int* nrow;
+    int nrow_max;
+    const int* fillq;
+    const int* fillslot;
+    const int* nfill;
+    int nfill_max;
+    double* scratch;
+    ScratchLayout lay;
+    double tol;
+    double zero_pivot;
+    int fill_cap;
+    unsigned long long* neg;
+    unsigned long long* minpiv;
+    int* err;
+    const int* active;
+};
+
+__device__ __forceinline__ double* slot_ptr(double* slots, int s, int lanes, int lane, int D) {
+    return slots + ((size_t)s * lanes + lane) * (size_t)D * D;
+}
+
+// element (i, j) of block (x, y) stored as (x, y) (trans = 0) or as (y, x) (trans = 1)
+__device__ __forceinline__ double& belem(double* B, int D, int trans, int i, int j) {
+    return trans ? B[(size_t)j * D + i] : B[(size_t)i * D + j];
+}
+
+__global__ void __launch_bounds__(NT) k_factor(FactorArgs A) {
+    const int ci = blockIdx.x, lane = blockIdx.y;
+    if (lane >= *A.active) return;
+    __shared__ double red[32];
+    __shared__ int redi[32];
+    __shared__ int s_neg, s_bad;
+    __shared__ double s_mp;
+    __shared__ int s_rk1;
+    const int D = A.D, LN = A.lanes;
+    const int p = A.cl[ci];
+    const int m = A.dim[p * LN + lane], r0 = A.rk[p * LN + lane];
+    double* scr = A.scratch + ((size_t)ci * LN + lane) * A.lay.total;
+    double* Z = scr + A.lay.z;
+    double* colnorm = scr + A.lay.colnorm;
+    double* Vr = scr + A.lay.vr;
+    double* Vq = scr + A.lay.vq;
+    double* tmp = scr + A.lay.tmp;
+    double* F = scr + A.lay.f;
+    int* perm = (int*)(scr + A.lay.iperm);
+    int* piv = perm + D;
+    int* hdr = (int*)(scr + A.lay.hdr);
+    int* hrows = hdr + 8;
+    double* Wb = scr + A.lay.w;
+    double* Yb = scr + A.lay.y;
+    auto live = [&](int x) {
+        return A.color[x] < A.cur_color ? A.rk[x * LN + lane] : A.dim[x * LN + lane];
+    };
+    if (threadIdx.x == 0) { s_neg = 0; s_bad = 0; s_mp = 1.0 / 0.0; s_rk1 = r0; }
+    __syncthreads();
+
+    // ---- (i) fill-in recompression of row p (Sec. 3.4) -------------------
+    const int R = m - r0;
+    const int nf = A.nfill[ci];
+    if (nf > 0 && R > 0) {
+        int wz = 0;
+        for (int f = 0; f < nf; ++f) wz += live(A.fillq[ci * A.nfill_max + f]);
+        int coff = 0;
+        for (int f = 0; f < nf; ++f) {
+            int q = A.fillq[ci * A.nfill_max + f];
+            int lq = live(q);
+            double* B = slot_ptr(A.slots, A.fillslot[ci * A.nfill_max + f], LN, lane, D);
+            int tr = p > q ? 0 : 1;
+            for (int e = threadIdx.x; e < R * lq; e += NT) {
+                int i = e / lq, j = e % lq;
+                Z[(size_t)i * wz + coff + j] = belem(B, D, tr, r0 + i, j);
+            }
+            coff += lq;
+        }
+        __syncthreads();
+        int capt = max(0, min(A.fill_cap, m) - r0);
+        int t = cta_pivqr<NT>(Z, wz, R, wz, A.tol, capt, Vr, D, colnorm, red, redi, &s_bad);
+        if (t > 0) {
+            cta_form_q<NT>(Vq, D, R, Vr, D, t);
+            const int nr = A.nrow[ci];
+            for (int b = 0; b < nr; ++b) {
+                int x = A.rowblk_other[ci * A.nrow_max + b];
+                int tr = A.rowblk_trans[ci * A.nrow_max + b];
+                double* B = slot_ptr(A.slots, A.rowblk[ci * A.nrow_max + b], LN, lane, D);
+                int dx = A.dim[x * LN + lane];
+                // rows r0.. of p: new = Vq^T old
+                for (int e = threadIdx.x; e < R * dx; e += NT) {
+                    int k = e / dx, j = e % dx;
+                    tmp[(size_t)k * D + j] = belem(B, D, tr, r0 + k, j);
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < R * dx; e += NT) {
+                    int i = e / dx, j = e % dx;
+                    double v = 0.0;
+                    for (int k = 0; k < R; ++k) v += Vq[(size_t)k * D + i] * tmp[(size_t)k * D + j];
+                    belem(B, D, tr, r0 + i, j) = v;
+                }
+                __syncthreads();
+                if (x == p) {   // diagonal block: columns r0.. as well
+                    for (int e = threadIdx.x; e < m * R; e += NT) {
+                        int i = e / R, k = e % R;
+                        tmp[(size_t)i * D + k] = B[(size_t)i * D + r0 + k];
+                    }
+                    __syncthreads();
+                    for (int e = threadIdx.x; e < m * R; e += NT) {
+                        int i = e / R, j = e % R;
+                        double v = 0.0;
+                        for (int k = 0; k < R; ++k) v += tmp[(size_t)i * D + k] * Vq[(size_t)k * D + j];
+                        B[(size_t)i * D + r0 + j] = v;
+                    }
+                    __syncthreads();
+                }
+            }
+        }
+        // drop the remaining redundant rows of the fill-in blocks
+        for (int f = 0; f < nf; ++f) {
+            int q = A.fillq[ci * A.nfill_max + f];
+            int dq = A.dim[q * LN + lane];
+            double* B = slot_ptr(A.slots, A.fillslot[ci * A.nfill_max + f], LN, lane, D);
+            int tr = p > q ? 0 : 1;
+            int rows = m - (r0 + t);
+            for (int e = threadIdx.x; e < rows * dq; e += NT) {
+                int i = e / dq, j = e % dq;
+                belem(B, D, tr, r0 + t + i, j) = 0.0;
+            }
+        }
+        if (threadIdx.x == 0) {
+            s_rk1 = r0 + t;
+            A.rk[p * LN + lane] = r0 + t;
+        }
+        __syncthreads();
+    }
+    const int rk1 = s_rk1;
+    const int Rp = m - rk1;
+    if (threadIdx.x == 0) {
+        hdr[0] = rk1;
+        hdr[1] = Rp;
+        if (s_bad) atomicOr(A.err, 1);
+    }
+    if (Rp <= 0) return;
+
+    // ---- (ii) Bunch-Kaufman LDL^T of S_pp^RR (Eq. blr2-diag-ldl) ------------
+    {
+        // the diagonal block is target 0 (a = p)
+        double* Bpp = slot_ptr(A.slots, A.targ_slot[ci * A.ntarg_max], LN, lane, D);
+        for (int e = threadIdx.x; e < Rp * Rp; e += NT) {
+            int i = e / Rp, j = e % Rp;
+            F[(size_t)i * D + j] = Bpp[(size_t)(rk1 + i) * D + rk1 + j];
+        }
+        __syncthreads();
+        cta_bk_ldl<NT>(F, D, Rp, perm, piv, red, redi, &s_neg, &s_mp, &s_bad, A.zero_pivot);
+        if (threadIdx.x == 0) {
+            atomicAdd(&A.neg[lane], (unsigned long long)s_neg);
+            double mp = s_mp;
+            if (!(mp >= 0.0)) mp = 0.0;
+            atomicMin(&A.minpiv[lane], (unsigned long long)__double_as_longlong(mp));
+            if (s_bad) atomicOr(A.err, 1);
+        }
+    }
+    // ---- (iii) W_a = S_ap^{.R} P L^{-T}, Y_a = W_a D^{-1} (Eq. blr2-diag-elimination)
+    const int nt = A.ntarg[ci];
+    for (int ti = threadIdx.x; ti < nt; ti += NT) {
+        int a = A.targ[ci * A.ntarg_max + ti];
+        hrows[ti] = (a == p) ? rk1 : live(a);
+    }
+    __syncthreads();
+    int total_rows = 0;
+    for (int ti = 0; ti < nt; ++ti) total_rows += hrows[ti];
+    for (int e = threadIdx.x; e < total_rows; e += NT) {
+        int ti = 0, i = e;
+        while (i >= hrows[ti]) { i -= hrows[ti]; ++ti; }
+        int tr = A.targ_trans[ci * A.ntarg_max + ti];
+        double* B = slot_ptr(A.slots, A.targ_slot[ci * A.ntarg_max + ti], LN, lane, D);
+        double* W = Wb + (size_t)ti * D * D + (size_t)i * D;
+        double* Y = Yb + (size_t)ti * D * D + (size_t)i * D;
+        for (int j = 0; j < Rp; ++j) {
+            double v = belem(B, D, tr, i, rk1 + perm[j]);
+            for (int k = 0; k < j; ++k) v -= W[k] * bk_L(F, D, piv, j, k);
+            W[j] = v;
+        }
+        for (int j = 0; j < Rp;) {
+            if (piv[j] == 1) {
+                Y[j] = W[j] / F[(size_t)j * D + j];
+                j += 1;
+            } else {
+                double a0 = F[(size_t)j * D + j], b0 = F[(size_t)(j + 1) * D + j],
+                       c0 = F[(size_t)(j + 1) * D + j + 1];
+                double det = a0 * c0 - b0 * b0;
+                double w0 = W[j], w1 = W[j + 1];
+                Y[j] = (w0 * c0 - w1 * b0) / det;
+                Y[j + 1] = (w1 * a0 - w0 * b0) / det;
+                j += 2;
+            }
+        }
+    }
+}
+
+struct SchurArgs {
+    double* slots;
+    int D, lanes;
+    const SchurPair* pairs;
+    int tiles_per_pair, tdim;
+    const double* scratch;
+    ScratchLayout lay;
+    const int* active;
+};
+
+// S_ab[i0:i0+32, j0:j0+32] -= W_a Y_b^T (Eq. blr2-diag-schur)
+__global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
+    const int lane = blockIdx.y;
+    if (lane >= *A.active) return;
+    const int pi = blockIdx.x / A.tiles_per_pair, tile = blockIdx.x % A.tiles_per_pair;
+    const SchurPair P = A.pairs[pi];
+    const int D = A.D;
+    const double* scr = A.scratch + ((size_t)P.elim * A.lanes + lane) * A.lay.total;
+    const int* hdr = (const int*)(scr + A.lay.hdr);
+    const int Rp = hdr[1];
+    if (Rp <= 0) return;
+    const int ra = hdr[8 + P.ta], rb = hdr[8 + P.tb];
+    const int i0 = (tile / A.tdim) * TS, j0 = (tile % A.tdim) * TS;
+    if (i0 >= ra || j0 >= rb) return;
+    const double* W = scr + A.lay.w + (size_t)P.ta * D * D;
+    const double* Y = scr + A.lay.y + (size_t)P.tb * D * D;
+    __shared__ double sW[TS][TS + 1], sY[TS][TS + 1];
+    const int tx = threadIdx.x % TS, ty = threadIdx.x / TS;   // ty in 0..7
+    double acc[4] = {0, 0, 0, 0};
+    for (int k0 = 0; k0 < Rp; k0 += TS) {
+        for (int e = threadIdx.x; e < TS * TS; e += NT) {
+            int r = e / TS, k = e % TS;
+            sW[r][k] = (i0 + r < ra && k0 + k < Rp) ? W[(size_t)(i0 + r) * D + k0 + k] : 0.0;
+            sY[r][k] = (j0 + r < rb && k0 + k < Rp) ? Y[(size_t)(j0 + r) * D + k0 + k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < TS; ++k) {
+            double y = sY[tx][k];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] += sW[ty + 8 * u][k] * y;
+        }
+        __syncthreads();
+    }
+    double* B = slot_ptr(A.slots, P.slot, A.lanes, lane, D);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int i = i0 + ty + 8 * u, j = j0 + tx;
+        if (i < ra && j < rb) belem(B, D, P.trans, i, j) -= acc[u];
+    }
+}
+
+// leaf level: copy Q^T A Q near blocks, subtract sigma on the diagonal, fill
+// blocks start as their coupling; dims/ranks from the build
+struct InitArgs {
+    double* slots;
+    int D, lanes;
+    const double* near_static;
+    const int* slot_a;
+    const int* slot_b;
+    const int* slot_kind;
+    const int* slot_far;
+    const double* C;
+    int rbl;
+    const int* rb;
+    const double* shifts;
+    const int* active;
+};
+
+__global__ void k_init_leaf(InitArgs A) {
+    const int sl = blockIdx.x, lane = blockIdx.y;
+    if (lane >= *A.active) return;
+    const int D = A.D;
+    double* B = slot_ptr(A.slots, sl, A.lanes, lane, D);
+    const int a = A.slot_a[sl], b = A.slot_b[sl];
+    if (A.slot_kind[sl] == 0) {
+        const double* S = A.near_static + (size_t)sl * D * D;
+        double sg = A.shifts[lane];
+        for (int e = threadIdx.x; e < D * D; e += NT) {
+            double v = S[e];
+            if (a == b && (e / D) == (e % D)) v -= sg;
+            B[e] = v;
+        }
+    } else {
+        const double* C = A.C + (size_t)A.slot_far[sl] * A.rbl * A.rbl;
+        int ra = A.rb[a], rbb = A.rb[b];
+        for (int e = threadIdx.x; e < D * D; e += NT) {
+            int i = e / D, j = e % D;
+            B[e] = (i < ra && j < rbb) ? C[(size_t)i * A.rbl + j] : 0.0;
+        }
+    }
+}
+
+__global__ void k_init_dims(int* dim, int* rk, const int64_t* off, const int* rb, int nc, int lanes,
+                            unsigned long long* neg, unsigned long long* minpiv, int* err) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nc * lanes) {
+        int c = e / lanes;
+        dim[e] = (int)(off[c + 1] - off[c]);
+        rk[e] = rb[c];
+    }
+    if (e < lanes) {
+        neg[e] = 0ull;
+        minpiv[e] = (unsigned long long)__double_as_longlong(1.0 / 0.0);
+    }
+    if (e == 0) *err = 0;
+}
+
+// parent dims: dim[P] = rk[c1] + rk[c2], rk[P] = rb[P]
+__global__ void k_merge_dims(int* dimP, int* rkP, const int* rkC, const int* rbP, int ncP, int lanes) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ncP * lanes) return;
+    int P = e / lanes, lane = e % lanes;
+    dimP[e] = rkC[(2 * P) * lanes + lane] + rkC[(2 * P + 1) * lanes + lane];
+    rkP[e] = rbP[P];
+}
+
+struct MergeArgs {
+    double* slotsP;
+    int DP, lanes;
+    const int* slotP_a;
+    const int* slotP_b;
+    const int* slotP_kind;
+    const int* slotP_far;
+    const double* CP;
+    int rblP;
+    const int* rbP;
+    const double* TP;
+    int dqP;
+    const double* slotsC;
+    int DC;
+    int ncC;
+    const int* slot_ofC;
+    const int* far_ofC;
+    const double* CC;
+    int rblC;
+    const int* rbC;
+    const int* rkC;
+    double* scratch;   // [nslotsP][lanes][2][DP*DP]
+    const int* active;
+};
+
+__device__ __forceinline__ int place_child(int first, int i, int rb_self, int rb1, int rb2, int t1) {
+    // parent coordinates [orig c1 | orig c2 | new c1 | new c2]
+    if (i < rb_self) return first ? i : rb1 + i;
+    return rb1 + rb2 + (first ? (i - rb_self) : t1 + (i - rb_self));
+}
+
+__global__ void __launch_bounds__(NT) k_merge(MergeArgs A) {
+    const int sl = blockIdx.x, lane = blockIdx.y;
+    if (lane >= *A.active) return;
+    const int DP = A.DP, LN = A.lanes;
+    double* out = slot_ptr(A.slotsP, sl, LN, lane, DP);
+    const int P = A.slotP_a[sl], Q = A.slotP_b[sl];
+    if (A.slotP_kind[sl] == 1) {
+        const double* C = A.CP + (size_t)A.slotP_far[sl] * A.rblP * A.rblP;
+        int ra = A.rbP[P], rq = A.rbP[Q];
+        for (int e = threadIdx.x; e < DP * DP; e += NT) {
+            int i = e / DP, j = e % DP;
+            out[e] = (i < ra && j < rq) ? C[(size_t)i * A.rblP + j] : 0.0;
+        }
+        return;
+    }
+    double* S = A.scratch + ((size_t)sl * LN + lane) * 2 * DP * DP;
+    double* M = S + (size_t)DP * DP;
+    int rkc[4], rbc[4];
+    const int cc[4] = {2 * P, 2 * P + 1, 2 * Q, 2 * Q + 1};
+    for (int u = 0; u < 4; ++u) {
+        rkc[u] = A.rkC[cc[u] * LN + lane];
+        rbc[u] = A.rbC[cc[u]];
+    }
+    const int dP = rkc[0] + rkc[1], dQ = rkc[2] + rkc[3];
+    const int kP = rbc[0] + rbc[1], kQ = rbc[2] + rbc[3];
+    for (int e = threadIdx.x; e < DP * DP; e += NT) S[e] = 0.0;
+    __syncthreads();
+    for (int u = 0; u < 2; ++u)
+        for (int v = 2; v < 4; ++v) {
+            const int c = cc[u], d = cc[v];
+            const int rc_ = rkc[u], rd_ = rkc[v];
+            const int sc = A.slot_ofC[(size_t)max(c, d) * A.ncC + min(c, d)];
+            for (int e = threadIdx.x; e < rc_ * rd_; e += NT) {
+                int i = e / rd_, j = e % rd_;
+                double val;
+                if (sc >= 0) {
+                    const double* B = A.slotsC + ((size_t)sc * LN + lane) * (size_t)A.DC * A.DC;
+                    val = c >= d ? B[(size_t)i * A.DC + j] : B[(size_t)j * A.DC + i];
+                } else {
+                    int fi = c > d ? A.far_ofC[(size_t)c * A.ncC + d] : A.far_ofC[(size_t)d * A.ncC + c];
+                    const double* C = A.CC + (size_t)fi * A.rblC * A.rblC;
+                    if (i < rbc[u] && j < rbc[v])
+                        val = c > d ? C[(size_t)i * A.rblC + j] : C[(size_t)j * A.rblC + i];
+                    else
+                        val = 0.0;
+                }
+                int pi_ = place_child(u == 0, i, rbc[u], rbc[0], rbc[1], rkc[0] - rbc[0]);
+                int pj_ = place_child(v == 2, j, rbc[v], rbc[2], rbc[3], rkc[2] - rbc[2]);
+                S[(size_t)pi_ * DP + pj_] = val;
+            }
+        }
+    __syncthreads();
+    const double* TPm = A.TP + (size_t)P * A.dqP * A.dqP;
+    const double* TQm = A.TP + (size_t)Q * A.dqP * A.dqP;
+    for (int e = threadIdx.x; e < dP * dQ; e += NT) {     // M = T_P^T S
+        int i = e / dQ, j = e % dQ;
+        double v;
+        if (i < kP) {
+            v = 0.0;
+            for (int k = 0; k < kP; ++k) v += TPm[(size_t)k * A.dqP + i] * S[(size_t)k * DP + j];
+        } else {
+            v = S[(size_t)i * DP + j];
+        }
+        M[(size_t)i * DP + j] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < DP * DP; e += NT) {     // out = M T_Q
+        int i = e / DP, j = e % DP;
+        double v = 0.0;
+        if (i < dP && j < dQ) {
+            if (j < kQ) {
+                for (int k = 0; k < kQ; ++k) v += M[(size_t)i * DP + k] * TQm[(size_t)k * A.dqP + j];
+            } else {
+                v = M[(size_t)i * DP + j];
+            }
+        }
+        out[e] = v;
+    }
+}
+
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+__global__ void k_finish(const unsigned long long* neg, const unsigned long long* minpiv, int64_t* counts,
+                         double* mp, const int* active) {
+    int lane = blockIdx.x * blockDim.x + threadIdx.x;
+    if (lane >= *active) return;
+    counts[lane] = (int64_t)neg[lane];
+    mp[lane] = __longlong_as_double((long long)minpiv[lane]);
+}
+
+// ------------------------------------------------------------ workspace --
+struct ColourDev {
+    int ncl, ntarg_max, nrow_max, nfill_max, npairs;
+    int *cl, *targ, *targ_slot, *targ_trans, *ntarg, *rowblk, *rowblk_other, *rowblk_trans, *nrow,
+        *fillq, *fillslot, *nfill;
+    SchurPair* pairs;
+};
+
+struct LevelWork {
+    std::vector<ColourDev> colours;
+    ScratchLayout lay;
+    int ncl_max = 0;
+    int* d_slot_of = nullptr;
+    int* d_far_of = nullptr;
+};
+
+struct FactorState {
+    std::vector<LevelWork> lw;
+    int* d_active = nullptr;
+    int64_t* d_counts = nullptr;
+    double* d_mp = nullptr;
+    double* d_lo = nullptr;   // bisection
+    double* d_hi = nullptr;
+    int64_t* d_k = nullptr;
+    int* d_nact = nullptr;
+    int nk_cap = 0;
+};
+
+static FactorState* state_of(h2_matrix* h) {
+    return reinterpret_cast<FactorState*>(h->ws.graph_state);
+}
+
+int alloc_workspace(h2_matrix* h, int lanes) {
+    const Plan& P = h->plan;
+    const int L = P.L;
+    Workspace& ws = h->ws;
+    ws.lanes = lanes;
+    auto* fs = new FactorState();
+    ws.graph_state = fs;
+    fs->lw.resize(L + 1);
+    int fill_cap = h->opt.fill_cap > 0 ? h->opt.fill_cap : 2 * h->rank;
+    h->fill_cap_eff = fill_cap;
+    // padded dims per level
+    for (int l = L; l >= 0; --l) {
+        LevelDev& D = h->lev[l];
+        if (l == L) D.dmax = std::max(1, h->mmax);
+        else {
+            const LevelDev& C = h->lev[l + 1];
+            int skc = std::max(C.rbmax, std::min(fill_cap, C.dmax));
+            D.dmax = std::max(1, 2 * skc);
+        }
+    }
+    size_t scratch_max = 0, merge_max = 0;
+    int rc;
+    for (int l = 0; l <= L; ++l) {
+        LevelDev& D = h->lev[l];
+        const LevelPlan& lp = P.lev[l];
+        LevelWork& W = fs->lw[l];
+        int nc = lp.nc;
+        int ntarg_max = 1, nrow_max = 1, nfill_max = 1;
+        for (int p = 0; p < nc; ++p) {
+            int nn = 0, nf = 0;
+            for (int x = 0; x < nc; ++x) {
+                nn += lp.is_near(p, x);
+                nf += lp.is_fill(p, x);
+            }
+            ntarg_max = std::max(ntarg_max, nn);
+            nrow_max = std::max(nrow_max, nn + nf);
+            nfill_max = std::max(nfill_max, nf);
+        }
+        W.lay = scratch_layout(D.dmax, nfill_max, ntarg_max);
+        for (const auto& cl : lp.color_lists) W.ncl_max = std::max<int>(W.ncl_max, (int)cl.size());
+        scratch_max = std::max(scratch_max, (size_t)W.ncl_max * lanes * W.lay.total);
+        if (l < L) merge_max = std::max(merge_max, (size_t)D.nslots * lanes * 2 * D.dmax * D.dmax);
+        // colour work lists
+        for (const auto& cl : lp.color_lists) {
+            ColourDev C{};
+            C.ncl = (int)cl.size();
+            C.ntarg_max = ntarg_max;
+            C.nrow_max = nrow_max;
+            C.nfill_max = nfill_max;
+            std::vector<int> targ(C.ncl * ntarg_max, -1), tslot(C.ncl * ntarg_max, -1),
+                ttr(C.ncl * ntarg_max, 0), ntarg(C.ncl), rowblk(C.ncl * nrow_max, -1),
+                rowother(C.ncl * nrow_max, -1), rowtr(C.ncl * nrow_max, 0), nrow(C.ncl),
+                fillq(C.ncl * nfill_max, -1), fillslot(C.ncl * nfill_max, -1), nfill(C.ncl);
+            std::vector<SchurPair> pairs;
+            auto slot = [&](int a, int b) { return D.slot_of[(size_t)std::max(a, b) * nc + std::min(a, b)]; };
+            for (int ci = 0; ci < C.ncl; ++ci) {
+                int p = cl[ci];
+                std::vector<int> tg{p};
+                for (int x = 0; x < nc; ++x)
+                    if (x != p && lp.is_near(p, x)) tg.push_back(x);
+                ntarg[ci] = (int)tg.size();
+                for (int ti = 0; ti < (int)tg.size(); ++ti) {
+                    int a = tg[ti];
+                    targ[ci * ntarg_max + ti] = a;
+                    tslot[ci * ntarg_max + ti] = slot(a, p);
+                    ttr[ci * ntarg_max + ti] = p > a ? 1 : 0;
+                }
+                for (int i = 0; i < (int)tg.size(); ++i)
+                    for (int j = 0; j <= i; ++j) {
+                        int a = tg[i], b = tg[j];
+                        pairs.push_back(SchurPair{ci, i, j, slot(a, b), a < b ? 1 : 0, a, b});
+                    }
+                int nr = 0, nfl = 0;
+                for (int x = 0; x < nc; ++x) {
+                    if (lp.is_near(p, x) || lp.is_fill(p, x)) {
+                        rowblk[ci * nrow_max + nr] = slot(p, x);
+                        rowother[ci * nrow_max + nr] = x;
+                        rowtr[ci * nrow_max + nr] = x > p ? 1 : 0;
+                        ++nr;
+                    }
+                    if (lp.is_fill(p, x)) {
+                        fillq[ci * nfill_max + nfl] = x;
+                        fillslot[ci * nfill_max + nfl] = slot(p, x);
+                        ++nfl;
+                    }
+                }
+                nrow[ci] = nr;
+                nfill[ci] = nfl;
+            }
+            C.npairs = (int)pairs.size();
+            if ((rc = upload(&C.cl, std::vector<int>(cl.begin(), cl.end()))) || (rc = upload(&C.targ, targ)) ||
+                (rc = upload(&C.targ_slot, tslot)) || (rc = upload(&C.targ_trans, ttr)) ||
+                (rc = upload(&C.ntarg, ntarg)) || (rc = upload(&C.rowblk, rowblk)) ||
+                (rc = upload(&C.rowblk_other, rowother)) || (rc = upload(&C.rowblk_trans, rowtr)) ||
+                (rc = upload(&C.nrow, nrow)) || (rc = upload(&C.fillq, fillq)) ||
+                (rc = upload(&C.fillslot, fillslot)) || (rc = upload(&C.nfill, nfill)) ||
+                (rc = upload(&C.pairs, pairs)))
+                return rc;
+            W.colours.push_back(C);
+        }
+        if ((rc = upload(&W.d_slot_of, D.slot_of)) || (rc = upload(&W.d_far_of, D.far_of))) return rc;
+    }
+    // buffers
+    ws.d_slots.assign(L + 1, nullptr);
+    ws.d_dim.assign(L + 1, nullptr);
+    ws.d_rk.assign(L + 1, nullptr);
+    size_t bytes = 0;
+    for (int l = 0; l <= L; ++l) {
+        LevelDev& D = h->lev[l];
+        size_t sz = (size_t)std::max(D.nslots, 1) * lanes * D.dmax * D.dmax;
+        if ((rc = dalloc(&ws.d_slots[l], sz))) return rc;
+        if ((rc = dalloc(&ws.d_dim[l], (size_t)D.nc * lanes))) return rc;
+        if ((rc = dalloc(&ws.d_rk[l], (size_t)D.nc * lanes))) return rc;
+        bytes += sz * 8 + (size_t)D.nc * lanes * 8;
+    }
+    if ((rc = dalloc(&ws.d_scratch, scratch_max))) return rc;
+    if ((rc = dalloc(&ws.d_merge, std::max<size_t>(merge_max, 1)))) return rc;
+    bytes += (scratch_max + merge_max) * 8;
+    if ((rc = dalloc(&ws.d_neg, lanes)) || (rc = dalloc(&ws.d_minpiv, lanes)) || (rc = dalloc(&ws.d_err, 4)) ||
+        (rc = dalloc(&ws.d_shifts, lanes)) || (rc = dalloc(&fs->d_active, 1)) ||
+        (rc = dalloc(&fs->d_counts, lanes)) || (rc = dalloc(&fs->d_mp, lanes)))
+        return rc;
+    ws.bytes = bytes;
+    return H2_OK;
+}
+
+// enqueue one full factorization of the workspace's lanes on stream st
+static void enqueue_factorization(h2_matrix* h, cudaStream_t st) {
+    const Plan& P = h->plan;
+    const int L = P.L;
+    Workspace& ws = h->ws;
+    FactorState* fs = state_of(h);
+    const int LN = ws.lanes;
+    {
+        LevelDev& D = h->lev[L];
+        int ne = std::max(D.nc * LN, LN);
+        k_init_dims<<<(ne + 255) / 256, 256, 0, st>>>(ws.d_dim[L], ws.d_rk[L], D.d_off, D.d_rb, D.nc, LN,
+                                                     ws.d_neg, ws.d_minpiv, ws.d_err);
+        InitArgs ia{ws.d_slots[L], D.dmax, LN, D.d_near_static, D.d_slot_a, D.d_slot_b, D.d_slot_kind,
+                    D.d_slot_far, D.d_C, D.estride, D.d_rb, ws.d_shifts, fs->d_active};
+        k_init_leaf<<<dim3(D.nslots, LN), NT, 0, st>>>(ia);
+    }
+    for (int l = L; l >= 0; --l) {
+        LevelDev& D = h->lev[l];
+        LevelWork& W = fs->lw[l];
+        for (int c = 0; c < (int)W.colours.size(); ++c) {
+            const ColourDev& C = W.colours[c];
+            FactorArgs fa{ws.d_slots[l], D.dmax, LN, ws.d_dim[l], ws.d_rk[l], D.d_color, c, C.cl, C.targ,
+                          C.targ_slot, C.targ_trans, C.ntarg, C.ntarg_max, C.rowblk, C.rowblk_other,
+                          C.rowblk_trans, C.nrow, C.nrow_max, C.fillq, C.fillslot, C.nfill, C.nfill_max,
+                          ws.d_scratch, W.lay, h->tol, 2.220446049250313e-16 * h->norm_inf,
+                          h->fill_cap_eff, ws.d_neg, ws.d_minpiv, ws.d_err,
+                          fs->d_active};
+            k_factor<<<dim3(C.ncl, LN), NT, 0, st>>>(fa);
+            int tdim = (D.dmax + TS - 1) / TS;
+            SchurArgs sa{ws.d_slots[l], D.dmax, LN, C.pairs, tdim * tdim, tdim, ws.d_scratch, W.lay,
+                         fs->d_active};
+            k_schur<<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
+        }
+        if (l > 0) {
+            LevelDev& Pd = h->lev[l - 1];
+            int ne = Pd.nc * LN;
+            k_merge_dims<<<(ne + 255) / 256, 256, 0, st>>>(ws.d_dim[l - 1], ws.d_rk[l - 1], ws.d_rk[l], Pd.d_rb,
+                                                          Pd.nc, LN);
+            MergeArgs ma{ws.d_slots[l - 1], Pd.dmax, LN, Pd.d_slot_a, Pd.d_slot_b, Pd.d_slot_kind,
+                         Pd.d_slot_far, Pd.d_C, Pd.estride, Pd.d_rb, Pd.d_Q, Pd.dq, ws.d_slots[l], D.dmax,
+                         D.nc, W.d_slot_of, W.d_far_of, D.d_C, D.estride, D.d_rb, ws.d_rk[l], ws.d_merge,
+                         fs->d_active};
+            k_merge<<<dim3(Pd.nslots, LN), NT, 0, st>>>(ma);
+        }
+    }
+    k_finish<<<(LN + 255) / 256, 256, 0, st>>>(ws.d_neg, ws.d_minpiv, fs->d_counts, fs->d_mp, fs->d_active);
+}
+
+static int ensure_graph(h2_matrix* h) {
+    Workspace& ws = h->ws;
+    if (ws.graph) return H2_OK;
+    cudaStream_t st = h->stream;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    enqueue_factorization(h, st);
+    CK(cudaStreamEndCapture(st, &g));
+    CK(cudaGraphInstantiate(&ws.graph, g, 0));
+    cudaGraphDestroy(g);
+    return H2_OK;
+}
+
+int run_inertia(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts, double* d_minpiv) {
+    Workspace& ws = h->ws;
+    FactorState* fs = state_of(h);
+    cudaStream_t st = h->stream;
+    if (ns <= 0) return H2_OK;
+    if (ns > ws.lanes) {
+        set_error("h2_inertia_device: ns exceeds max_lanes");
+        return H2_ERR_INVALID_ARG;
+    }
+    int rc = ensure_graph(h);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ws.d_shifts, d_shifts, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    k_set_int<<<1, 1, 0, st>>>(fs->d_active, ns);
+    CK(cudaGraphLaunch(ws.graph, st));
+    CK(cudaMemcpyAsync(d_counts, fs->d_counts, ns * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    if (d_minpiv) CK(cudaMemcpyAsync(d_minpiv, fs->d_mp, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return H2_OK;
+}
+
+// host arrays: each batch of <= lanes shifts is copied in, factorized and its
+// counts copied back (the end-to-end path of h2_inertia)
+int run_inertia_host(h2_matrix* h, const double* shifts, int64_t ns, int64_t* counts, double* minpiv) {
+    Workspace& ws = h->ws;
+    FactorState* fs = state_of(h);
+    cudaStream_t st = h->stream;
+    int rc = ensure_graph(h);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(ws.d_err, 0, sizeof(int), st));
+    for (int64_t b0 = 0; b0 < ns; b0 += ws.lanes) {
+        int nb = (int)std::min<int64_t>(ws.lanes, ns - b0);
+        CK(cudaMemcpyAsync(ws.d_shifts, shifts + b0, nb * sizeof(double), cudaMemcpyHostToDevice, st));
+        k_set_int<<<1, 1, 0, st>>>(fs->d_active, nb);
+        CK(cudaGraphLaunch(ws.graph, st));
+        CK(cudaMemcpyAsync(counts + b0, fs->d_counts, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        if (minpiv) CK(cudaMemcpyAsync(minpiv + b0, fs->d_mp, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        int err = 0;
+        CK(cudaMemcpyAsync(&err, ws.d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (err) {
+            set_error("h2_inertia: NaN pivot in the factorization");
+            return H2_ERR_NUMERICAL;
+        }
+    }
+    return H2_OK;
+}
+
+// --------------------------------------------------------------- bisection --
+// plan: distinct active intervals get the lanes; each gets q points
+// lo + (hi-lo) j/(q+1), j = 1..q
+__global__ void k_bisect_plan(const double* lo, const double* hi, int nk, double tol, int lanes,
+                              double* shifts, int* active, int* nact) {
+    __shared__ int s_first[1024];
+    // distinct active intervals in k order (O(nk^2) dedupe, nk small)
+    if (threadIdx.x == 0) {
+        int nd = 0;
+        for (int k = 0; k < nk; ++k) {
+            if (!(hi[k] - lo[k] >= tol)) continue;
+            bool dup = false;
+            for (int u = 0; u < nd && !dup; ++u) {
+                int k2 = s_first[u];
+                dup = (lo[k2] == lo[k] && hi[k2] == hi[k]);
+            }
+            if (!dup && nd < 1024) s_first[nd++] = k;
+        }
+        *nact = nd;
+        int used = 0;
+        if (nd > 0) {
+            int m = min(nd, lanes);
+            int q = lanes / m, extra = lanes % m;
+            for (int u = 0; u < m; ++u) {
+                int qu = q + (u < extra ? 1 : 0);
+                int k = s_first[u];
+                double a = lo[k], b = hi[k];
+                for (int j = 1; j <= qu; ++j) shifts[used++] = a + (b - a) * (double)j / (double)(qu + 1);
+            }
+        }
+        *active = used;
+    }
+}
+
+__global__ void k_bisect_update(double* lo, double* hi, const int64_t* kk, int nk, const double* shifts,
+                                const int64_t* counts, const int* active) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nk) return;
+    double a = lo[k], b = hi[k];
+    int64_t kv = kk[k];
+    int ns = *active;
+    for (int i = 0; i < ns; ++i) {
+        double mu = shifts[i];
+        if (a < mu && mu < b) {
+            if (counts[i] >= kv) b = mu;
+            else a = mu;
+        }
+    }
+    lo[k] = a;
+    hi[k] = b;
+}
+
+int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out, double* err_bound) {
+    Workspace& ws = h->ws;
+    FactorState* fs = state_of(h);
+    cudaStream_t st = h->stream;
+    int rc = ensure_graph(h);
+    if (rc) return rc;
+    if (nk > 1024) {
+        set_error("h2_kth_eig: at most 1024 k per call");
+        return H2_ERR_INVALID_ARG;
+    }
+    // start interval: Gershgorin padded by 1e-6 ||A||_inf; check nu(a) = 0, nu(b) = n
+    double a = h->glo - 1e-6 * h->norm_inf, b = h->ghi + 1e-6 * h->norm_inf;
+    {
+        double sh[2] = {a, b};
+        int two = std::min(2, ws.lanes);
+        CK(cudaMemcpyAsync(ws.d_shifts, sh, two * sizeof(double), cudaMemcpyHostToDevice, st));
+        k_set_int<<<1, 1, 0, st>>>(fs->d_active, two);
+        CK(cudaGraphLaunch(ws.graph, st));
+        int64_t cnt[2] = {0, 0};
+        CK(cudaMemcpyAsync(cnt, fs->d_counts, two * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (two == 2 && (cnt[0] != 0 || cnt[1] != h->n)) {
+            set_error("h2_kth_eig: nu(a) != 0 or nu(b) != n on the Gershgorin interval");
+            return H2_ERR_INTERVAL;
+        }
+    }
+    if (fs->nk_cap < nk) {
+        cudaFree(fs->d_lo); cudaFree(fs->d_hi); cudaFree(fs->d_k); cudaFree(fs->d_nact);
+        if ((rc = dalloc(&fs->d_lo, nk)) || (rc = dalloc(&fs->d_hi, nk)) || (rc = dalloc(&fs->d_k, nk)) ||
+            (rc = dalloc(&fs->d_nact, 1)))
+            return rc;
+        fs->nk_cap = (int)nk;
+    }
+    std::vector<double> lo(nk, a), hi(nk, b);
+    CK(cudaMemcpyAsync(fs->d_lo, lo.data(), nk * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(fs->d_hi, hi.data(), nk * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(fs->d_k, k, nk * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    int rounds = 0;
+    h->last_rounds = 0;
+    h->last_shifts = 0;
+    while (true) {
+        k_bisect_plan<<<1, 32, 0, st>>>(fs->d_lo, fs->d_hi, (int)nk, tol, ws.lanes, ws.d_shifts, fs->d_active,
+                                        fs->d_nact);
+        int nact = 0, used = 0;
+        CK(cudaMemcpyAsync(&nact, fs->d_nact, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&used, fs->d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (nact == 0) break;
+        CK(cudaGraphLaunch(ws.graph, st));
+        k_bisect_update<<<(unsigned)((nk + 127) / 128), 128, 0, st>>>(fs->d_lo, fs->d_hi, fs->d_k, (int)nk,
+                                                                     ws.d_shifts, fs->d_counts, fs->d_active);
+        ++rounds;
+        h->last_shifts += used;
+        if (rounds > 4096) {
+            set_error("h2_kth_eig: bisection did not converge");
+            return H2_ERR_NUMERICAL;
+        }
+    }
+    h->last_rounds = rounds;
+    CK(cudaMemcpyAsync(lo.data(), fs->d_lo, nk * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hi.data(), fs->d_hi, nk * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, ws.d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err) {
+        set_error("h2_kth_eig: NaN pivot in the factorization");
+        return H2_ERR_NUMERICAL;
+    }
+    for (int64_t i = 0; i < nk; ++i) {
+        out[i] = 0.5 * (lo[i] + hi[i]);
+        if (err_bound) err_bound[i] = 0.5 * (hi[i] - lo[i]);
+    }
+    return H2_OK;
+}
+
+void free_workspace(h2_matrix* h) {
+    Workspace& ws = h->ws;
+    if (ws.graph) cudaGraphExecDestroy(ws.graph);
+    ws.graph = nullptr;
+    for (auto p : ws.d_slots) cudaFree(p);
+    for (auto p : ws.d_dim) cudaFree(p);
+    for (auto p : ws.d_rk) cudaFree(p);
+    cudaFree(ws.d_scratch); cudaFree(ws.d_merge); cudaFree(ws.d_neg); cudaFree(ws.d_minpiv);
+    cudaFree(ws.d_err); cudaFree(ws.d_shifts);
+    FactorState* fs = state_of(h);
+    if (fs) {
+        for (auto& W : fs->lw) {
+            for (auto& C : W.colours) {
+                cudaFree(C.cl); cudaFree(C.targ); cudaFree(C.targ_slot); cudaFree(C.targ_trans);
+                cudaFree(C.ntarg); cudaFree(C.rowblk); cudaFree(C.rowblk_other); cudaFree(C.rowblk_trans);
+                cudaFree(C.nrow); cudaFree(C.fillq); cudaFree(C.fillslot); cudaFree(C.nfill); cudaFree(C.pairs);
+            }
+            cudaFree(W.d_slot_of); cudaFree(W.d_far_of);
+        }
+        cudaFree(fs->d_active); cudaFree(fs->d_counts); cudaFree(fs->d_mp);
+        cudaFree(fs->d_lo); cudaFree(fs->d_hi); cudaFree(fs->d_k); cudaFree(fs->d_nact);
+        delete fs;
+    }
+    ws.graph_state = nullptr;
+}
+
+}  // namespace h2
