@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the generalized H^2-LDL^T inertia path on GB300.
+
+Workload (the n = 1024 configuration): n = 1024 points uniform in the unit
+square (SplitMix64 seed 1), A_ij = 1/(|x_i - x_j| + 1e-3) (A_ii = 1e3), leaf
+64, rank 16, eta = 1 (box admissibility), FP64.  A step is one batch of 64
+shifted matrices A~ - sigma I factorized together (all levels: leaf blocks,
+fill-in recompression, Bunch-Kaufman LDL^T, Schur updates, merges, negative
+pivot count); the shifts of step i are 64 points spread over the Gershgorin
+interval (seeded jitter), resident in HBM before the timed region.
+
+value : LDL-inertia shifts/sec, device-resident shifts (h2_inertia_device).
+e2e   : the same metric through h2_inertia with host (pinned) buffers: the H2D
+        copy of the 64 shifts and the D2H read of the 64 counts in every step.
+Extra keys: k-th eigenvalue solves (k = n/2, tol 1e-8) -- eigs/sec, p50/p99
+latency, rounds, shifts per solve.
+
+Multi-GPU (torchrun): every rank holds its own replica and factorizes its own
+batches (independent shifts, no data-path collective); value = all ranks'
+shifts / max-over-ranks time ("scaling": "weak").
+
+--impl reference times the CPU oracle (the plain FP64 generalized H^2-LDL) on
+the host cores on the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = dict(name="laplace2d_n1024", n=1024, d=2, seed=1, kernel=W.LAPLACE_EPS,
+                kparams=(1e-3, 0.0, 0.0, 0.0), leaf=64, rank=16, eta=1.0, k=512, tol=1e-8)
+METRIC = "LDL-inertia shifts/sec (FP64); k-th eigs/sec at tol 1e-8 with p50/p99"
+FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 (profiling recipe table); not in MEASURED_PEAKS
+# DRAM traffic of one k_schur launch from the committed ncu capture, valid while
+# the factorization source is unchanged (sha256 prefix recorded with it)
+NCU_TRAFFIC = {"kernel": "k_schur", "bytes_per_launch": None, "source_sha": None}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _source_sha():
+    h = hashlib.sha256()
+    for f in ("h2_factor.cu", "h2_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2311_08618_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _shift_batches(lo, hi, lanes, count, seed=7):
+    """count batches of lanes shifts spread over [lo, hi] with seeded jitter."""
+    u = W.uniform(seed, count * lanes).reshape(count, lanes)
+    base = (np.arange(lanes)[None, :] + u) / lanes
+    return lo + (hi - lo) * base
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    import torch
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local, dist
+
+
+def _max_over_ranks(x, dist, device):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ------------------------------------------------------------- CPU oracle --
+def _oracle_worker(args):
+    """Spawned worker: builds the oracle H^2 matrix, waits, times its shifts."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    wl, warm, shifts, barrier = args
+    sys.path.insert(0, ROOT)
+    import workloads as Wk
+    from oracle import h2 as oh2
+    X = Wk.uniform_cube(wl["n"], wl["d"], wl["seed"])
+    h = oh2.construct(X, wl["kernel"], wl["kparams"], wl["leaf"], wl["rank"], wl["eta"])
+    for s in warm:
+        oh2.h2_inertia(h, s)
+    barrier.wait()
+    t0 = time.time()
+    counts = [oh2.h2_inertia(h, s)[0] for s in shifts]
+    return t0, time.time(), counts
+
+
+def oracle_throughput(shifts, cores, warm=()):
+    """Shifts/sec of the oracle over `shifts`, one process per core (spawn);
+    each worker first evaluates its share of `warm` untimed."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    env_before = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_before:
+        os.environ[k] = "1"
+    try:
+        mgr = ctx.Manager()
+        bar = mgr.Barrier(cores)
+        parts = [list(shifts[i::cores]) for i in range(cores)]
+        wparts = [list(warm[i::cores]) for i in range(cores)]
+        with ctx.Pool(cores) as pool:
+            res = pool.map(_oracle_worker, [(WORKLOAD, w, p, bar) for w, p in zip(wparts, parts)])
+    finally:
+        for k, v in env_before.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    t0 = min(r[0] for r in res)
+    t1 = max(r[1] for r in res)
+    counts = {}
+    for p, r in zip(parts, res):
+        for s, c in zip(p, r[2]):
+            counts[s] = c
+    return len(shifts) / (t1 - t0), t1 - t0, counts
+
+
+def reference_arm(args, rank, world, dist):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    from oracle import dense
+    X = W.uniform_cube(WORKLOAD["n"], WORKLOAD["d"], WORKLOAD["seed"])
+    A = dense.kernel_matrix(WORKLOAD["kernel"], WORKLOAD["kparams"], X)
+    lo, hi = dense.gershgorin(A)
+    per_step = cores                      # one shift per core per step
+    total = args.warmup + args.steps
+    batches = _shift_batches(lo, hi, per_step, total, seed=11)
+    rate, secs, _ = oracle_throughput(list(batches[args.warmup:].ravel()), cores,
+                                      warm=list(batches[:args.warmup].ravel()))
+    ms_step = secs / args.steps * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "shifts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "leaf": 64, "rank": 16, "eta": 1.0,
+                       "shifts_per_step": per_step},
+            "cpu_baseline": {"value": rate, "unit": "shifts/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d shifts of the %s workload, one process per core"
+                                       % (per_step * args.steps, WORKLOAD["name"])},
+            "e2e": {"value": rate, "unit": "shifts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- our path --
+def ours(args, rank, world, local, dist):
+    import torch
+    import paper_2311_08618_gb300 as pkg
+    from paper_2311_08618_gb300 import build
+    if rank == 0:
+        build.build()
+    _barrier(dist)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    lanes = args.lanes
+    X = W.uniform_cube(WORKLOAD["n"], WORKLOAD["d"], WORKLOAD["seed"])
+    t0 = time.time()
+    M = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
+                     eta=WORKLOAD["eta"], max_lanes=lanes, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    info = M.h2_info()
+    lo, hi = info["gershgorin_lo"], info["gershgorin_hi"]
+    total = args.warmup + args.steps
+    sh = _shift_batches(lo, hi, lanes, total, seed=7 + rank)
+    d_sh = torch.tensor(sh, dtype=torch.float64, device=dev)
+    d_cnt = torch.zeros((total, lanes), dtype=torch.int64, device=dev)
+    d_mp = torch.zeros((total, lanes), dtype=torch.float64, device=dev)
+    # ---- device-resident timed region
+    for i in range(args.warmup):
+        M.h2_inertia_device(d_sh[i], lanes, d_cnt[i], d_mp[i])
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    _barrier(dist)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.warmup, total):
+        M.h2_inertia_device(d_sh[i], lanes, d_cnt[i], d_mp[i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(dist)
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = _max_over_ranks(ms, dist, dev)
+    value = world * args.steps * lanes / (ms_max / 1e3)
+    # ---- end to end: host (pinned) shifts in, host counts out, every step
+    h_sh = torch.tensor(sh, dtype=torch.float64).pin_memory()
+    h_cnt = torch.zeros((total, lanes), dtype=torch.int64).pin_memory()
+    L = pkg.lib()
+    import ctypes as C
+
+    def e2e_step(i):
+        rc = L.h2_inertia(M._h, C.c_void_p(h_sh[i].data_ptr()), lanes, C.c_void_p(h_cnt[i].data_ptr()), None)
+        if rc != 0:
+            raise RuntimeError(L.h2_last_error().decode())
+
+    for i in range(args.warmup):
+        e2e_step(i)
+    _barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.warmup, total):
+        e2e_step(i)
+    torch.cuda.synchronize()
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, dist, dev)
+    _barrier(dist)
+    e2e_value = world * args.steps * lanes / e2e_s
+    same = bool(torch.equal(d_cnt.cpu(), h_cnt))
+    # ---- k-th eigenvalue solves (all of the path incl. the bisection driver)
+    lat = []
+    lam = None
+    for i in range(args.eig_solves + 2):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out, eb = M.h2_kth_eig([WORKLOAD["k"]], WORKLOAD["tol"])
+        lat.append(time.perf_counter() - t)
+        lam = (out[0], eb[0])
+    lat = np.array(lat[2:])
+    info2 = M.h2_info()
+    # ---- roofline of the dominant kernel: profiled batches (events per launch)
+    prof = None
+    for i in range(args.warmup, min(total, args.warmup + 5)):
+        p = M.h2_profile_batch(d_sh[i], lanes, d_cnt[i])
+        if prof is None:
+            prof = p
+        else:
+            for k in prof:
+                for f in ("ms", "flops", "bytes"):
+                    prof[k][f] += p[k][f]
+                prof[k]["launches"] += p[k]["launches"]
+    dom = max(("factor", "schur", "merge", "init"), key=lambda k: prof[k]["ms"])
+    tot_ms = sum(v["ms"] for v in prof.values())
+    pk = prof[dom]
+    per_launch_ms = pk["ms"] / pk["launches"]
+    flops_launch = pk["flops"] / pk["launches"]
+    bytes_launch = pk["bytes"] / pk["launches"]
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6746.0)
+    fp64_gf = FP64_PEAK_GFLOPS
+    ai = flops_launch / max(bytes_launch, 1.0)
+    if ai > fp64_gf / hbm:
+        achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_gf / 1e3, "unit": "TFLOP/s",
+                "frac": achieved / (fp64_gf / 1e3), "peak_source": "nominal FP64 (recipe table; not measured)"}
+    else:
+        achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": "measured hbm_gbs"}
+    traffic = None
+    if NCU_TRAFFIC["bytes_per_launch"] and NCU_TRAFFIC["kernel"] == "k_" + dom and \
+            NCU_TRAFFIC["source_sha"] == _source_sha():
+        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    roof.update({"kernel": "k_" + dom, "traffic": traffic, "flops_per_launch": flops_launch,
+                 "bytes_per_launch": bytes_launch, "launch_ms": per_launch_ms,
+                 "share_of_batch": pk["ms"] / tot_ms,
+                 "kernel_shares": {k: v["ms"] / tot_ms for k, v in prof.items()}})
+    ws_mb = info["workspace_bytes"] / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "shifts/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "n": WORKLOAD["n"], "leaf": WORKLOAD["leaf"],
+                       "rank": WORKLOAD["rank"], "eta": WORKLOAD["eta"], "admissibility": "box",
+                       "shifts_per_step": lanes, "parallelism": "replica per GPU",
+                       "l2": "per-step working set %.0f MB > 129 MB L2" % ws_mb},
+            "e2e": {"value": e2e_value, "unit": "shifts/s", "h2d_bytes_per_step": 8 * lanes,
+                    "d2h_bytes_per_step": 8 * lanes, "counts_match_device_path": same},
+            "gpu_launches": info["kernels_per_batch"] * args.steps,
+            "eigs": {"k": WORKLOAD["k"], "tol": WORKLOAD["tol"], "eigs_per_s": float(1.0 / np.mean(lat)),
+                     "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                     "rounds": info2["last_rounds"], "shifts_per_solve": info2["last_shifts"],
+                     "lambda": lam[0], "err_bound": lam[1]},
+            "build_s": build_s, "roofline": roof, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        sample = list(sh[args.warmup][:: max(1, lanes // (2 * cores))][:2 * cores])
+        rate, secs, ocounts = oracle_throughput(sample, cores)
+        got = {s: int(c) for s, c in zip(sh[args.warmup], d_cnt[args.warmup].cpu().numpy())}
+        agree = sum(int(got[s] == ocounts[s]) for s in sample)
+        line["cpu_baseline"] = {"value": rate, "unit": "shifts/s", "cores": cores, "kind": "oracle",
+                                "sample": "%d shifts of step 1 (%.1f s wall, one process per core)" %
+                                          (len(sample), secs),
+                                "counts_equal_to_gpu": "%d/%d" % (agree, len(sample))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    M.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lanes", type=int, default=64)
+    ap.add_argument("--eig-solves", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local, dist = _dist()
+    try:
+        if args.impl == "reference":
+            reference_arm(args, rank, world, dist)
+        else:
+            ours(args, rank, world, local, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

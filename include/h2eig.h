@@ -152,9 +152,31 @@ typedef struct {
     double trunc_tol;        /* eps_h2 * ||A||_inf */
     int64_t workspace_bytes; /* per-batch factorization workspace */
     int lanes;               /* shifts per batch */
+    int kernels_per_batch;   /* kernel launches of one batch (CUDA graph nodes) */
+    int last_rounds;         /* bisection rounds of the last h2_kth_eig */
+    int64_t last_shifts;     /* shifts evaluated by the last h2_kth_eig */
 } h2_stats;
 
 int h2_info(h2_handle h, h2_stats* out);
+
+/*
+ * h2_profile_batch -- measurement aid.  Runs one batch of ns <= max_lanes
+ * device-resident shifts like h2_inertia_device but without the CUDA graph,
+ * recording CUDA events around every kernel launch on the handle's stream, and
+ * blocks until done.  Per kernel kind j (H2_KIND_*): ms[j] = summed device time
+ * of its launches, launches[j] = their number, flops[j] = algorithmic FP64
+ * flops and bytes[j] = algorithmic bytes moved (operands read once, results
+ * written once; see the design notes for the per-unit formulas).
+ * All four arrays: host, caller-owned, H2_NKINDS entries.  d_counts: device, ns.
+ */
+#define H2_KIND_INIT   0   /* leaf blocks of A~ - sigma I                   */
+#define H2_KIND_FACTOR 1   /* recompression + BK LDL^T + triangular solves  */
+#define H2_KIND_SCHUR  2   /* Schur-complement updates                       */
+#define H2_KIND_MERGE  3   /* merge into the parent level + transfer bases  */
+#define H2_KIND_OTHER  4   /* dims, counts                                   */
+#define H2_NKINDS      5
+int h2_profile_batch(h2_handle h, const double* d_shifts, int64_t ns, int64_t* d_counts,
+                     double* ms, int64_t* launches, double* flops, double* bytes);
 
 /* tree order: perm[i] = index (0-based, in the input) of the i-th point in
  * tree order.  perm: host, caller-owned, n int64. */

@@ -17,7 +17,9 @@ H2_K_LAPLACE_EPS, H2_K_YUKAWA_EPS, H2_K_GAUSS_PLUS_INV, H2_K_TRIDIAG_TEST, H2_K_
 H2_ADM_BOX, H2_ADM_CENTER = 0, 1
 
 EXPORTED_SYMBOLS = ["h2_default_options", "h2_build", "h2_destroy", "h2_last_error", "h2_inertia",
-                    "h2_inertia_device", "h2_kth_eig", "h2_info", "h2_tree_perm", "h2_level_ranks"]
+                    "h2_inertia_device", "h2_kth_eig", "h2_info", "h2_tree_perm", "h2_level_ranks",
+                    "h2_profile_batch"]
+KIND_NAMES = ["init", "factor", "schur", "merge", "other"]
 
 
 class Kernel(C.Structure):
@@ -34,7 +36,8 @@ class Stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("levels", C.c_int), ("leaves", C.c_int), ("max_rank", C.c_int),
                 ("near_pairs", C.c_int64), ("fill_pairs", C.c_int64), ("norm_inf", C.c_double),
                 ("gershgorin_lo", C.c_double), ("gershgorin_hi", C.c_double), ("trunc_tol", C.c_double),
-                ("workspace_bytes", C.c_int64), ("lanes", C.c_int)]
+                ("workspace_bytes", C.c_int64), ("lanes", C.c_int), ("kernels_per_batch", C.c_int),
+                ("last_rounds", C.c_int), ("last_shifts", C.c_int64)]
 
 
 class H2Error(RuntimeError):
@@ -72,8 +75,9 @@ def lib():
         L.h2_info.argtypes = [P, C.POINTER(Stats)]
         L.h2_tree_perm.argtypes = [P, P]
         L.h2_level_ranks.argtypes = [P, C.c_int, P]
+        L.h2_profile_batch.argtypes = [P, P, C.c_int64, P, P, P, P, P]
         for f in ("h2_build", "h2_inertia", "h2_inertia_device", "h2_kth_eig", "h2_info",
-                  "h2_tree_perm", "h2_level_ranks"):
+                  "h2_tree_perm", "h2_level_ranks", "h2_profile_batch"):
             getattr(L, f).restype = C.c_int
         _LIB = L
     return _LIB
@@ -139,6 +143,18 @@ class H2Matrix:
 
     def h2_inertia_device(self, d_shifts, ns, d_counts, d_minpiv=None):
         _check(lib().h2_inertia_device(self._h, _ptr(d_shifts), int(ns), _ptr(d_counts), _ptr(d_minpiv)))
+
+    def h2_profile_batch(self, d_shifts, ns, d_counts):
+        """Per kernel kind: (ms, launches, flops, bytes) of one profiled batch."""
+        ms = np.zeros(5)
+        nl = np.zeros(5, dtype=np.int64)
+        fl = np.zeros(5)
+        by = np.zeros(5)
+        _check(lib().h2_profile_batch(self._h, _ptr(d_shifts), int(ns), _ptr(d_counts),
+                                      ms.ctypes.data_as(C.c_void_p), nl.ctypes.data_as(C.c_void_p),
+                                      fl.ctypes.data_as(C.c_void_p), by.ctypes.data_as(C.c_void_p)))
+        return {k: {"ms": float(ms[i]), "launches": int(nl[i]), "flops": float(fl[i]), "bytes": float(by[i])}
+                for i, k in enumerate(KIND_NAMES)}
 
     def h2_kth_eig(self, ks, tol):
         k = np.ascontiguousarray(ks, dtype=np.int64).ravel()

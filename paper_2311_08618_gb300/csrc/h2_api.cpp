@@ -158,7 +158,20 @@ int h2_info(h2_handle h, h2_stats* s) {
     s->trunc_tol = h->tol;
     s->workspace_bytes = (int64_t)h->ws.bytes;
     s->lanes = h->ws.lanes;
+    s->kernels_per_batch = h->kernels_per_batch;
+    s->last_rounds = h->last_rounds;
+    s->last_shifts = h->last_shifts;
     return H2_OK;
+}
+
+int h2_profile_batch(h2_handle h, const double* d_shifts, int64_t ns, int64_t* d_counts, double* ms,
+                     int64_t* launches, double* flops, double* bytes) {
+    g_last_error.clear();
+    if (!h || !d_shifts || !d_counts || !ms || !launches || !flops || !bytes) {
+        set_error("h2_profile_batch: null pointer");
+        return H2_ERR_INVALID_ARG;
+    }
+    return run_profile(h, d_shifts, (int)ns, d_counts, ms, launches, flops, bytes);
 }
 
 int h2_tree_perm(h2_handle h, int64_t* perm) {

@@ -112,6 +112,7 @@ struct FactorArgs {
     unsigned long long* minpiv;
     int* err;
     const int* active;
+    double* stats;   // [2 * H2_NKINDS]: algorithmic flops, then bytes, per kernel kind
 };
 
 __device__ __forceinline__ double* slot_ptr(double* slots, int s, int lanes, int lane, int D) {
@@ -174,6 +175,18 @@ __global__ void __launch_bounds__(NT) k_factor(FactorArgs A) {
         __syncthreads();
         int capt = max(0, min(A.fill_cap, m) - r0);
         int t = cta_pivqr<NT>(Z, wz, R, wz, A.tol, capt, Vr, D, colnorm, red, redi, &s_bad);
+        if (threadIdx.x == 0) {
+            double fl = 4.0 * R * (double)wz * t + 4.0 * (double)R * R * t;
+            double by = 8.0 * 2.0 * R * (double)wz;
+            if (t > 0) {
+                double sdx = 0.0;
+                for (int b = 0; b < A.nrow[ci]; ++b) sdx += A.dim[A.rowblk_other[ci * A.nrow_max + b] * LN + lane];
+                fl += 2.0 * R * (double)R * sdx + 2.0 * m * (double)R * R;
+                by += 8.0 * (2.0 * R * sdx + 2.0 * m * (double)R);
+            }
+            atomicAdd(&A.stats[H2_KIND_FACTOR], fl);
+            atomicAdd(&A.stats[H2_NKINDS + H2_KIND_FACTOR], by);
+        }
         if (t > 0) {
             cta_form_q<NT>(Vq, D, R, Vr, D, t);
             const int nr = A.nrow[ci];
@@ -265,6 +278,22 @@ __global__ void __launch_bounds__(NT) k_factor(FactorArgs A) {
     __syncthreads();
     int total_rows = 0;
     for (int ti = 0; ti < nt; ++ti) total_rows += hrows[ti];
+    if (threadIdx.x == 0) {
+        double R3 = (double)Rp * Rp * Rp / 3.0;
+        double fl = R3 + (double)total_rows * Rp * Rp + (double)total_rows * Rp;
+        double by = 8.0 * ((double)Rp * Rp + 3.0 * (double)total_rows * Rp);
+        double fs = 0.0, bs = 0.0;
+        for (int i = 0; i < nt; ++i)
+            for (int j = 0; j <= i; ++j) {
+                double ra = hrows[i], rb = hrows[j];
+                fs += 2.0 * ra * rb * Rp;
+                bs += 8.0 * (ra * Rp + rb * Rp + 2.0 * ra * rb);
+            }
+        atomicAdd(&A.stats[H2_KIND_FACTOR], fl);
+        atomicAdd(&A.stats[H2_NKINDS + H2_KIND_FACTOR], by);
+        atomicAdd(&A.stats[H2_KIND_SCHUR], fs);
+        atomicAdd(&A.stats[H2_NKINDS + H2_KIND_SCHUR], bs);
+    }
     for (int e = threadIdx.x; e < total_rows; e += NT) {
         int ti = 0, i = e;
         while (i >= hrows[ti]) { i -= hrows[ti]; ++ti; }
@@ -361,6 +390,7 @@ struct InitArgs {
     const int* rb;
     const double* shifts;
     const int* active;
+    double* stats;
 };
 
 __global__ void k_init_leaf(InitArgs A) {
@@ -369,6 +399,7 @@ __global__ void k_init_leaf(InitArgs A) {
     const int D = A.D;
     double* B = slot_ptr(A.slots, sl, A.lanes, lane, D);
     const int a = A.slot_a[sl], b = A.slot_b[sl];
+    if (threadIdx.x == 0) atomicAdd(&A.stats[H2_NKINDS + H2_KIND_INIT], 16.0 * D * (double)D);
     if (A.slot_kind[sl] == 0) {
         const double* S = A.near_static + (size_t)sl * D * D;
         double sg = A.shifts[lane];
@@ -388,7 +419,7 @@ __global__ void k_init_leaf(InitArgs A) {
 }
 
 __global__ void k_init_dims(int* dim, int* rk, const int64_t* off, const int* rb, int nc, int lanes,
-                            unsigned long long* neg, unsigned long long* minpiv, int* err) {
+                            unsigned long long* neg, unsigned long long* minpiv, int* err, double* stats) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < nc * lanes) {
         int c = e / lanes;
@@ -400,6 +431,7 @@ __global__ void k_init_dims(int* dim, int* rk, const int64_t* off, const int* rb
         minpiv[e] = (unsigned long long)__double_as_longlong(1.0 / 0.0);
     }
     if (e == 0) *err = 0;
+    if (e < 2 * H2_NKINDS) stats[e] = 0.0;
 }
 
 // parent dims: dim[P] = rk[c1] + rk[c2], rk[P] = rb[P]
@@ -434,6 +466,7 @@ struct MergeArgs {
     const int* rkC;
     double* scratch;   // [nslotsP][lanes][2][DP*DP]
     const int* active;
+    double* stats;
 };
 
 __device__ __forceinline__ int place_child(int first, int i, int rb_self, int rb1, int rb2, int t1) {
@@ -467,6 +500,11 @@ __global__ void __launch_bounds__(NT) k_merge(MergeArgs A) {
     }
     const int dP = rkc[0] + rkc[1], dQ = rkc[2] + rkc[3];
     const int kP = rbc[0] + rbc[1], kQ = rbc[2] + rbc[3];
+    if (threadIdx.x == 0) {
+        atomicAdd(&A.stats[H2_KIND_MERGE], 2.0 * kP * (double)kP * dQ + 2.0 * dP * (double)kQ * kQ);
+        atomicAdd(&A.stats[H2_NKINDS + H2_KIND_MERGE],
+                  8.0 * (2.0 * dP * (double)dQ + (double)kP * kP + (double)kQ * kQ + (double)DP * DP));
+    }
     for (int e = threadIdx.x; e < DP * DP; e += NT) S[e] = 0.0;
     __syncthreads();
     for (int u = 0; u < 2; ++u)
@@ -553,6 +591,7 @@ struct FactorState {
     int* d_active = nullptr;
     int64_t* d_counts = nullptr;
     double* d_mp = nullptr;
+    double* d_stats = nullptr;  // [2 * H2_NKINDS]
     double* d_lo = nullptr;   // bisection
     double* d_hi = nullptr;
     int64_t* d_k = nullptr;
@@ -684,27 +723,56 @@ int alloc_workspace(h2_matrix* h, int lanes) {
     bytes += (scratch_max + merge_max) * 8;
     if ((rc = dalloc(&ws.d_neg, lanes)) || (rc = dalloc(&ws.d_minpiv, lanes)) || (rc = dalloc(&ws.d_err, 4)) ||
         (rc = dalloc(&ws.d_shifts, lanes)) || (rc = dalloc(&fs->d_active, 1)) ||
-        (rc = dalloc(&fs->d_counts, lanes)) || (rc = dalloc(&fs->d_mp, lanes)))
+        (rc = dalloc(&fs->d_counts, lanes)) || (rc = dalloc(&fs->d_mp, lanes)) ||
+        (rc = dalloc(&fs->d_stats, 2 * H2_NKINDS)))
         return rc;
     ws.bytes = bytes;
     return H2_OK;
 }
 
-// enqueue one full factorization of the workspace's lanes on stream st
-static void enqueue_factorization(h2_matrix* h, cudaStream_t st) {
+// Event pairs around launches (profiling mode of enqueue_factorization).
+struct Profiler {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+    size_t used = 0;
+    cudaStream_t st = nullptr;
+    void before(int k) {
+        if (used + 2 > ev.size()) {
+            for (int i = 0; i < 64; ++i) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                ev.push_back(e);
+            }
+        }
+        kind.push_back(k);
+        cudaEventRecord(ev[used++], st);
+    }
+    void after() { cudaEventRecord(ev[used++], st); }
+};
+
+// enqueue one full factorization of the workspace's lanes on stream st;
+// returns the number of kernel launches
+static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof = nullptr) {
     const Plan& P = h->plan;
     const int L = P.L;
     Workspace& ws = h->ws;
     FactorState* fs = state_of(h);
     const int LN = ws.lanes;
+    int nl = 0;
+    auto B = [&](int k) { ++nl; if (prof) prof->before(k); };
+    auto E = [&]() { if (prof) prof->after(); };
     {
         LevelDev& D = h->lev[L];
-        int ne = std::max(D.nc * LN, LN);
+        int ne = std::max(std::max(D.nc * LN, LN), 2 * H2_NKINDS);
+        B(H2_KIND_OTHER);
         k_init_dims<<<(ne + 255) / 256, 256, 0, st>>>(ws.d_dim[L], ws.d_rk[L], D.d_off, D.d_rb, D.nc, LN,
-                                                     ws.d_neg, ws.d_minpiv, ws.d_err);
+                                                     ws.d_neg, ws.d_minpiv, ws.d_err, fs->d_stats);
+        E();
         InitArgs ia{ws.d_slots[L], D.dmax, LN, D.d_near_static, D.d_slot_a, D.d_slot_b, D.d_slot_kind,
-                    D.d_slot_far, D.d_C, D.estride, D.d_rb, ws.d_shifts, fs->d_active};
+                    D.d_slot_far, D.d_C, D.estride, D.d_rb, ws.d_shifts, fs->d_active, fs->d_stats};
+        B(H2_KIND_INIT);
         k_init_leaf<<<dim3(D.nslots, LN), NT, 0, st>>>(ia);
+        E();
     }
     for (int l = L; l >= 0; --l) {
         LevelDev& D = h->lev[l];
@@ -715,27 +783,37 @@ static void enqueue_factorization(h2_matrix* h, cudaStream_t st) {
                           C.targ_slot, C.targ_trans, C.ntarg, C.ntarg_max, C.rowblk, C.rowblk_other,
                           C.rowblk_trans, C.nrow, C.nrow_max, C.fillq, C.fillslot, C.nfill, C.nfill_max,
                           ws.d_scratch, W.lay, h->tol, 2.220446049250313e-16 * h->norm_inf,
-                          h->fill_cap_eff, ws.d_neg, ws.d_minpiv, ws.d_err,
-                          fs->d_active};
+                          h->fill_cap_eff, ws.d_neg, ws.d_minpiv, ws.d_err, fs->d_active, fs->d_stats};
+            B(H2_KIND_FACTOR);
             k_factor<<<dim3(C.ncl, LN), NT, 0, st>>>(fa);
+            E();
             int tdim = (D.dmax + TS - 1) / TS;
             SchurArgs sa{ws.d_slots[l], D.dmax, LN, C.pairs, tdim * tdim, tdim, ws.d_scratch, W.lay,
                          fs->d_active};
+            B(H2_KIND_SCHUR);
             k_schur<<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
+            E();
         }
         if (l > 0) {
             LevelDev& Pd = h->lev[l - 1];
             int ne = Pd.nc * LN;
+            B(H2_KIND_OTHER);
             k_merge_dims<<<(ne + 255) / 256, 256, 0, st>>>(ws.d_dim[l - 1], ws.d_rk[l - 1], ws.d_rk[l], Pd.d_rb,
                                                           Pd.nc, LN);
+            E();
             MergeArgs ma{ws.d_slots[l - 1], Pd.dmax, LN, Pd.d_slot_a, Pd.d_slot_b, Pd.d_slot_kind,
                          Pd.d_slot_far, Pd.d_C, Pd.estride, Pd.d_rb, Pd.d_Q, Pd.dq, ws.d_slots[l], D.dmax,
                          D.nc, W.d_slot_of, W.d_far_of, D.d_C, D.estride, D.d_rb, ws.d_rk[l], ws.d_merge,
-                         fs->d_active};
+                         fs->d_active, fs->d_stats};
+            B(H2_KIND_MERGE);
             k_merge<<<dim3(Pd.nslots, LN), NT, 0, st>>>(ma);
+            E();
         }
     }
+    B(H2_KIND_OTHER);
     k_finish<<<(LN + 255) / 256, 256, 0, st>>>(ws.d_neg, ws.d_minpiv, fs->d_counts, fs->d_mp, fs->d_active);
+    E();
+    return nl;
 }
 
 static int ensure_graph(h2_matrix* h) {
@@ -744,7 +822,7 @@ static int ensure_graph(h2_matrix* h) {
     cudaStream_t st = h->stream;
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    enqueue_factorization(h, st);
+    h->kernels_per_batch = enqueue_factorization(h, st);
     CK(cudaStreamEndCapture(st, &g));
     CK(cudaGraphInstantiate(&ws.graph, g, 0));
     cudaGraphDestroy(g);
@@ -767,6 +845,41 @@ int run_inertia(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts,
     CK(cudaGraphLaunch(ws.graph, st));
     CK(cudaMemcpyAsync(d_counts, fs->d_counts, ns * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
     if (d_minpiv) CK(cudaMemcpyAsync(d_minpiv, fs->d_mp, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return H2_OK;
+}
+
+int run_profile(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts, double* ms,
+                int64_t* launches, double* flops, double* bytes) {
+    Workspace& ws = h->ws;
+    FactorState* fs = state_of(h);
+    cudaStream_t st = h->stream;
+    if (ns <= 0 || ns > ws.lanes) {
+        set_error("h2_profile_batch: need 1 <= ns <= max_lanes");
+        return H2_ERR_INVALID_ARG;
+    }
+    CK(cudaMemcpyAsync(ws.d_shifts, d_shifts, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    k_set_int<<<1, 1, 0, st>>>(fs->d_active, ns);
+    Profiler pr;
+    pr.st = st;
+    int nl = enqueue_factorization(h, st, &pr);
+    CK(cudaMemcpyAsync(d_counts, fs->d_counts, ns * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    double stats[2 * H2_NKINDS];
+    CK(cudaMemcpyAsync(stats, fs->d_stats, sizeof(stats), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int k = 0; k < H2_NKINDS; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+        flops[k] = stats[k];
+        bytes[k] = stats[H2_NKINDS + k];
+    }
+    for (size_t i = 0; i < pr.kind.size(); ++i) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, pr.ev[2 * i], pr.ev[2 * i + 1]));
+        ms[pr.kind[i]] += t;
+        launches[pr.kind[i]] += 1;
+    }
+    for (auto e : pr.ev) cudaEventDestroy(e);
+    (void)nl;
     return H2_OK;
 }
 
@@ -943,7 +1056,7 @@ void free_workspace(h2_matrix* h) {
             }
             cudaFree(W.d_slot_of); cudaFree(W.d_far_of);
         }
-        cudaFree(fs->d_active); cudaFree(fs->d_counts); cudaFree(fs->d_mp);
+        cudaFree(fs->d_active); cudaFree(fs->d_counts); cudaFree(fs->d_mp); cudaFree(fs->d_stats);
         cudaFree(fs->d_lo); cudaFree(fs->d_hi); cudaFree(fs->d_k); cudaFree(fs->d_nact);
         delete fs;
     }

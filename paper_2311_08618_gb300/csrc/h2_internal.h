@@ -138,6 +138,7 @@ struct h2_matrix {
     int fill_cap_eff = 0;          // skeleton cap after recompression
     int last_rounds = 0;           // bisection rounds of the last h2_kth_eig
     int64_t last_shifts = 0;       // shifts evaluated by the last h2_kth_eig
+    int kernels_per_batch = 0;     // launches in one batch (graph nodes)
 };
 
 namespace h2 {
@@ -148,6 +149,8 @@ int run_inertia(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts,
                 double* d_minpiv);                    // enqueue one batch
 int run_inertia_host(h2_matrix* h, const double* shifts, int64_t ns, int64_t* counts,
                      double* minpiv);
+int run_profile(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts, double* ms,
+                int64_t* launches, double* flops, double* bytes);
 int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
             double* err_bound);
 void free_workspace(h2_matrix* h);
