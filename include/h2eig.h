@@ -178,6 +178,39 @@ int h2_info(h2_handle h, h2_stats* out);
 int h2_profile_batch(h2_handle h, const double* d_shifts, int64_t ns, int64_t* d_counts,
                      double* ms, int64_t* launches, double* flops, double* bytes);
 
+/*
+ * h2_dense_inertia_noalloc -- counts[i] = #{negative pivots} of a
+ * Bunch-Kaufman LDL^T of A - shifts[i] I for a small DENSE symmetric matrix A
+ * (the same kernel routine the H^2 factorization uses for its diagonal
+ * blocks), and min_abs_pivot[i] as in h2_inertia, WITHOUT allocating any
+ * memory.  The paper has no counterpart to this entry point.  It is for
+ * callers that cannot call cudaMalloc: code that records a CUDA graph (an
+ * allocation is not allowed while a stream is being captured), code that must
+ * not add the device-wide synchronization an allocation can cause (for
+ * example inside a latency-critical serving loop), and code that runs under a
+ * fixed, pre-reserved memory budget.
+ *   d_A             : device, n x n row-major FP64, leading dimension lda >= n;
+ *                     only read; the full matrix is read and must be symmetric.
+ *   d_shifts        : device, ns FP64.
+ *   d_counts        : device, caller-owned, ns int64.
+ *   d_min_abs_pivot : device, caller-owned, ns FP64, or NULL.
+ *   stream          : cudaStream_t to enqueue on, NULL for the default stream.
+ * Working memory is one static device array of H2_NOALLOC_MAX_DOUBLES doubles
+ * (8 MiB) inside the library, which every GPU that loads the library holds
+ * until the process exits.  A call uses ns * n * n doubles of it and returns
+ * H2_ERR_INVALID_ARG, touching nothing, when that exceeds the maximum or when
+ * n < 1, n > 1024, ns < 1, ns > 1024 or lda < n.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call shares
+ * the array: calls that overlap on the GPU (on different streams or from
+ * different threads) race and give wrong results.  Each call overwrites every
+ * scratch element it reads, so nothing needs clearing between calls.
+ * Asynchronous: returns once the kernel is enqueued.
+ */
+#define H2_NOALLOC_MAX_DOUBLES 1048576
+int h2_dense_inertia_noalloc(const double* d_A, int n, int lda, const double* d_shifts, int ns,
+                             int64_t* d_counts, double* d_min_abs_pivot, void* stream);
+
 /* tree order: perm[i] = index (0-based, in the input) of the i-th point in
  * tree order.  perm: host, caller-owned, n int64. */
 int h2_tree_perm(h2_handle h, int64_t* perm);

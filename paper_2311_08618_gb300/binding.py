@@ -18,7 +18,7 @@ H2_ADM_BOX, H2_ADM_CENTER = 0, 1
 
 EXPORTED_SYMBOLS = ["h2_default_options", "h2_build", "h2_destroy", "h2_last_error", "h2_inertia",
                     "h2_inertia_device", "h2_kth_eig", "h2_info", "h2_tree_perm", "h2_level_ranks",
-                    "h2_profile_batch"]
+                    "h2_profile_batch", "h2_dense_inertia_noalloc"]
 KIND_NAMES = ["init", "factor", "schur", "merge", "other"]
 
 
@@ -76,6 +76,8 @@ def lib():
         L.h2_tree_perm.argtypes = [P, P]
         L.h2_level_ranks.argtypes = [P, C.c_int, P]
         L.h2_profile_batch.argtypes = [P, P, C.c_int64, P, P, P, P, P]
+        L.h2_dense_inertia_noalloc.argtypes = [P, C.c_int, C.c_int, P, C.c_int, P, P, P]
+        L.h2_dense_inertia_noalloc.restype = C.c_int
         for f in ("h2_build", "h2_inertia", "h2_inertia_device", "h2_kth_eig", "h2_info",
                   "h2_tree_perm", "h2_level_ranks", "h2_profile_batch"):
             getattr(L, f).restype = C.c_int
