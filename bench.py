@@ -323,7 +323,7 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
                 for f in ("ms", "flops", "bytes"):
                     prof[k][f] += p[k][f]
                 prof[k]["launches"] += p[k]["launches"]
-    dom = max(("factor", "schur", "merge", "init"), key=lambda k: prof[k]["ms"])
+    dom = max((k for k in prof if k != "other" and prof[k]["launches"] > 0), key=lambda k: prof[k]["ms"])
     tot_ms = sum(v["ms"] for v in prof.values())
     pk = prof[dom]
     per_launch_ms = pk["ms"] / pk["launches"]
@@ -349,6 +349,34 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
                  "bytes_per_launch": bytes_launch, "launch_ms": per_launch_ms,
                  "share_of_batch": pk["ms"] / tot_ms,
                  "kernel_shares": {k: v["ms"] / tot_ms for k, v in prof.items()}})
+    # ---- precision variant: FP32 Schur/rotation products, FP64 pivots/counts
+    Mx = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
+                      eta=WORKLOAD["eta"], max_lanes=lanes, stream=stream.cuda_stream,
+                      precision=pkg.H2_PREC_MIXED)
+    for i in range(args.warmup):
+        Mx.h2_inertia_device(d_sh[i], lanes, d_cnt[i], d_mp[i])
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(args.warmup, total):
+        Mx.h2_inertia_device(d_sh[i], lanes, d_cnt[i], d_mp[i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_mix = _max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    latm = []
+    for i in range(args.eig_solves + 2):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        outm, ebm = Mx.h2_kth_eig([WORKLOAD["k"]], WORKLOAD["tol"])
+        latm.append(time.perf_counter() - t)
+    latm = np.array(latm[2:])
+    infm = Mx.h2_info()
+    precision = {"mode": "fp32 products, fp64 storage/pivots/counts",
+                 "value": world * args.steps * lanes / (ms_mix / 1e3), "unit": "shifts/s",
+                 "eigs_per_s": float(1.0 / np.mean(latm)), "p50_ms": float(np.percentile(latm, 50) * 1e3),
+                 "p99_ms": float(np.percentile(latm, 99) * 1e3), "rounds": infm["last_rounds"],
+                 "mixed_rounds": infm["last_mixed_rounds"], "bracket_resets": infm["bracket_resets"],
+                 "lambda": float(outm[0]), "abs_diff_vs_fp64": float(abs(outm[0] - lam[0]))}
+    Mx.close()
     ws_mb = info["workspace_bytes"] / 1e6
     line = {"metric": METRIC, "value": value, "unit": "shifts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -364,7 +392,7 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
                      "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                      "rounds": info2["last_rounds"], "shifts_per_solve": info2["last_shifts"],
                      "lambda": lam[0], "err_bound": lam[1]},
-            "build_s": build_s, "roofline": roof, "clocks": clocks}
+            "build_s": build_s, "roofline": roof, "clocks": clocks, "precision": precision}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         sample = list(sh[args.warmup][:: max(1, lanes // (2 * cores))][:2 * cores])

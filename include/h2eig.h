@@ -59,9 +59,13 @@ typedef struct {
 #define H2_ADM_CENTER 1  /* (diam c + diam d)/2 <= eta * |center c - center d| */
 
 #define H2_PREC_FP64  0  /* every step in FP64 */
+#define H2_PREC_MIXED 1  /* Schur-update and rotation products in FP32 (FP32
+                            accumulation); storage, Bunch-Kaufman pivoting,
+                            pivot counts and interval updates in FP64; guarded
+                            shifts re-run in FP64 (see h2_inertia, h2_kth_eig) */
 
 typedef struct {
-    int precision;       /* H2_PREC_FP64 */
+    int precision;       /* H2_PREC_FP64 (default) or H2_PREC_MIXED */
     int admissibility;   /* H2_ADM_BOX (default) or H2_ADM_CENTER */
     double eps_h2;       /* truncation tolerance relative to ||A||_inf (Sec. 3.1,
                             eps_H2; default 1e-10 = 1e-2 * 1e-8, Sec. 5) */
@@ -70,6 +74,8 @@ typedef struct {
     int sketch_cols;     /* columns of the random sketch of A_{l;c,+}; 0 = rank + 16 */
     uint64_t seed;       /* SplitMix64 state for the sketch matrix */
     int max_lanes;       /* shifts factorized concurrently; 0 = 64 */
+    double pivot_guard;  /* mixed precision: a shift whose min |pivot| is below
+                            pivot_guard * ||A||_inf is re-run in FP64; 0 = 1e-4 */
     void* stream;        /* cudaStream_t for all work of the handle; NULL = a
                             stream created by the library */
 } h2_options;
@@ -111,13 +117,18 @@ const char* h2_last_error(void);
  *   counts        : host, caller-owned, ns int64.
  *   min_abs_pivot : host, caller-owned, ns FP64, or NULL.
  * Shifts are processed in batches of max_lanes.  Blocks until done.
+ * H2_PREC_MIXED: each batch is factorized with FP32 Schur/rotation products;
+ * a shift whose min |pivot| is below pivot_guard * ||A||_inf is factorized
+ * again in FP64 and its count and pivot replaced.
  */
 int h2_inertia(h2_handle h, const double* shifts, int64_t ns, int64_t* counts,
                double* min_abs_pivot);
 
 /*
  * h2_inertia_device -- as h2_inertia with DEVICE pointers; enqueued on the
- * handle's stream and returns without waiting (ns <= max_lanes).
+ * handle's stream and returns without waiting (ns <= max_lanes).  In
+ * H2_PREC_MIXED it returns the mixed counts without the FP64 re-run: the
+ * caller applies the guard with the returned min |pivot|.
  */
 int h2_inertia_device(h2_handle h, const double* d_shifts, int64_t ns, int64_t* d_counts,
                       double* d_min_abs_pivot);
@@ -129,6 +140,10 @@ int h2_inertia_device(h2_handle h, const double* d_shifts, int64_t ns, int64_t* 
  * interval (|lambda_k - lambda~_k| < tol/2, Eq. error-bound).  Every evaluated
  * (mu, nu) narrows every k (Sec. 4.2); each round spreads max_lanes shifts
  * over the distinct active intervals.  The intervals stay on the device.
+ * H2_PREC_MIXED: mixed rounds (guarded as in h2_inertia) run while the
+ * brackets are wider than Delta = 64 * 2^-24 * ||A||_inf; every bracket is
+ * then widened by Delta and checked in FP64 (nu(lo) < k <= nu(hi), else it
+ * restarts from the Gershgorin interval), and FP64 rounds finish to tol.
  *   k         : host, nk int64, 1-based, each in 1..n.
  *   tol > 0   : absolute interval width.
  *   out       : host, caller-owned, nk FP64.
@@ -155,6 +170,9 @@ typedef struct {
     int kernels_per_batch;   /* kernel launches of one batch (CUDA graph nodes) */
     int last_rounds;         /* bisection rounds of the last h2_kth_eig */
     int64_t last_shifts;     /* shifts evaluated by the last h2_kth_eig */
+    int last_mixed_rounds;   /* of those rounds, the mixed-precision ones */
+    int64_t last_guarded;    /* shifts re-run in FP64 by the last h2_inertia/h2_kth_eig */
+    int64_t bracket_resets;  /* mixed brackets that failed their FP64 check (total) */
 } h2_stats;
 
 int h2_info(h2_handle h, h2_stats* out);
@@ -170,11 +188,14 @@ int h2_info(h2_handle h, h2_stats* out);
  * All four arrays: host, caller-owned, H2_NKINDS entries.  d_counts: device, ns.
  */
 #define H2_KIND_INIT   0   /* leaf blocks of A~ - sigma I                   */
-#define H2_KIND_FACTOR 1   /* recompression + BK LDL^T + triangular solves  */
-#define H2_KIND_SCHUR  2   /* Schur-complement updates                       */
-#define H2_KIND_MERGE  3   /* merge into the parent level + transfer bases  */
-#define H2_KIND_OTHER  4   /* dims, counts                                   */
-#define H2_NKINDS      5
+#define H2_KIND_RECOMP 1   /* fill-in recompression basis (pivoted QR)      */
+#define H2_KIND_ROTATE 2   /* rotation of a row's blocks, fill truncation   */
+#define H2_KIND_LDL    3   /* Bunch-Kaufman LDL^T of S^RR, pivot count      */
+#define H2_KIND_TRSM   4   /* S^{xR} P L^-T and D^-1 for each coupled block */
+#define H2_KIND_SCHUR  5   /* Schur-complement updates                       */
+#define H2_KIND_MERGE  6   /* merge into the parent level + transfer bases  */
+#define H2_KIND_OTHER  7   /* dims, counts                                   */
+#define H2_NKINDS      8
 int h2_profile_batch(h2_handle h, const double* d_shifts, int64_t ns, int64_t* d_counts,
                      double* ms, int64_t* launches, double* flops, double* bytes);
 

@@ -15,11 +15,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 H2_K_LAPLACE_EPS, H2_K_YUKAWA_EPS, H2_K_GAUSS_PLUS_INV, H2_K_TRIDIAG_TEST, H2_K_MIN_TEST = 0, 1, 2, 3, 4
 H2_ADM_BOX, H2_ADM_CENTER = 0, 1
+H2_PREC_FP64, H2_PREC_MIXED = 0, 1
 
 EXPORTED_SYMBOLS = ["h2_default_options", "h2_build", "h2_destroy", "h2_last_error", "h2_inertia",
                     "h2_inertia_device", "h2_kth_eig", "h2_info", "h2_tree_perm", "h2_level_ranks",
                     "h2_profile_batch", "h2_dense_inertia_noalloc"]
-KIND_NAMES = ["init", "factor", "schur", "merge", "other"]
+KIND_NAMES = ["init", "recomp", "rotate", "ldl", "trsm", "schur", "merge", "other"]
 
 
 class Kernel(C.Structure):
@@ -29,7 +30,7 @@ class Kernel(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("admissibility", C.c_int), ("eps_h2", C.c_double),
                 ("fill_cap", C.c_int), ("sketch_cols", C.c_int), ("seed", C.c_uint64),
-                ("max_lanes", C.c_int), ("stream", C.c_void_p)]
+                ("max_lanes", C.c_int), ("pivot_guard", C.c_double), ("stream", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -37,7 +38,8 @@ class Stats(C.Structure):
                 ("near_pairs", C.c_int64), ("fill_pairs", C.c_int64), ("norm_inf", C.c_double),
                 ("gershgorin_lo", C.c_double), ("gershgorin_hi", C.c_double), ("trunc_tol", C.c_double),
                 ("workspace_bytes", C.c_int64), ("lanes", C.c_int), ("kernels_per_batch", C.c_int),
-                ("last_rounds", C.c_int), ("last_shifts", C.c_int64)]
+                ("last_rounds", C.c_int), ("last_shifts", C.c_int64), ("last_mixed_rounds", C.c_int),
+                ("last_guarded", C.c_int64), ("bracket_resets", C.c_int64)]
 
 
 class H2Error(RuntimeError):
@@ -148,10 +150,11 @@ class H2Matrix:
 
     def h2_profile_batch(self, d_shifts, ns, d_counts):
         """Per kernel kind: (ms, launches, flops, bytes) of one profiled batch."""
-        ms = np.zeros(5)
-        nl = np.zeros(5, dtype=np.int64)
-        fl = np.zeros(5)
-        by = np.zeros(5)
+        nk = len(KIND_NAMES)
+        ms = np.zeros(nk)
+        nl = np.zeros(nk, dtype=np.int64)
+        fl = np.zeros(nk)
+        by = np.zeros(nk)
         _check(lib().h2_profile_batch(self._h, _ptr(d_shifts), int(ns), _ptr(d_counts),
                                       ms.ctypes.data_as(C.c_void_p), nl.ctypes.data_as(C.c_void_p),
                                       fl.ctypes.data_as(C.c_void_p), by.ctypes.data_as(C.c_void_p)))

@@ -39,6 +39,7 @@ void h2_default_options(h2_options* opt) {
     opt->sketch_cols = 0;
     opt->seed = 0x5EEDull;
     opt->max_lanes = 64;
+    opt->pivot_guard = 1e-4;
     opt->stream = nullptr;
 }
 
@@ -57,7 +58,9 @@ int h2_build(const double* points, int64_t n, int d, h2_kernel kernel, int leaf,
     h2_default_options(&o);
     if (opt) o = *opt;
     if (o.max_lanes <= 0) o.max_lanes = 64;
-    if (!(o.eps_h2 >= 0.0) || o.fill_cap < 0 || o.sketch_cols < 0 || o.precision != H2_PREC_FP64 ||
+    if (!(o.pivot_guard > 0.0)) o.pivot_guard = 1e-4;
+    if (!(o.eps_h2 >= 0.0) || o.fill_cap < 0 || o.sketch_cols < 0 ||
+        (o.precision != H2_PREC_FP64 && o.precision != H2_PREC_MIXED) ||
         (o.admissibility != H2_ADM_BOX && o.admissibility != H2_ADM_CENTER)) {
         set_error("h2_build: invalid options");
         return H2_ERR_INVALID_ARG;
@@ -161,6 +164,9 @@ int h2_info(h2_handle h, h2_stats* s) {
     s->kernels_per_batch = h->kernels_per_batch;
     s->last_rounds = h->last_rounds;
     s->last_shifts = h->last_shifts;
+    s->last_mixed_rounds = h->last_mixed_rounds;
+    s->last_guarded = h->last_guarded;
+    s->bracket_resets = h->last_bracket_resets;
     return H2_OK;
 }
 

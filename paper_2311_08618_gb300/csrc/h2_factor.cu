@@ -4,12 +4,15 @@
 //
 // One batch factorizes `lanes` shifted matrices A~ - sigma_b I at once.  Per
 // level (leaves first) and per colour of the level's distance-2 colouring:
-//   k_factor : one CTA per (cluster p of the colour, lane): fill-in
-//              recompression of row p (pivoted QR of the fill-in blocks'
-//              redundant rows, rotation of p's redundant coordinates), the
-//              Bunch-Kaufman LDL^T of S_pp^RR with its negative-pivot count,
-//              and W_a = S_ap^{.R} P L^{-T}, Y_a = W_a D^{-1} for every block
-//              coupled to p's redundant part (Eqs. blr2-diag-ldl, -elimination);
+//   k_recomp : one CTA per (cluster p, lane): pivoted QR of the redundant rows
+//              of p's fill-in blocks -> rotation V of p's redundant coordinates
+//              (recompression, Sec. 3.4);
+//   k_rotate : one CTA per (block of row p, lane): apply V to that block, drop
+//              the truncated rows of fill-in blocks;
+//   k_ldl    : one CTA per (cluster, lane): Bunch-Kaufman LDL^T of S_pp^RR and
+//              its negative-pivot count (Eq. blr2-diag-ldl);
+//   k_trsm   : one CTA per (coupled block a, lane): W_a = S_ap^{.R} P L^{-T},
+//              Y_a = W_a D^{-1} (Eq. blr2-diag-elimination);
 //   k_schur  : S_ab -= W_a Y_b^T on every pair of those blocks (Eq. blr2-diag-schur),
 //              tiled 32 x 32 per CTA;
 // then k_merge gathers the children's skeleton blocks into the parent level
@@ -97,6 +100,7 @@ struct FactorArgs {
     const int* rowblk;
     const int* rowblk_other;
     const int* rowblk_trans;
+    const int* rowblk_fill;
     const int* nrow;
     int nrow_max;
     const int* fillq;
@@ -124,14 +128,28 @@ __device__ __forceinline__ double& belem(double* B, int D, int trans, int i, int
     return trans ? B[(size_t)j * D + i] : B[(size_t)i * D + j];
 }
 
-__global__ void __launch_bounds__(NT) k_factor(FactorArgs A) {
+// rows of cluster x still in the trailing matrix: all of them until x is
+// eliminated, its skeleton afterwards
+__device__ __forceinline__ int live_rows(const FactorArgs& A, int x, int lane) {
+    return A.color[x] < A.cur_color ? A.rk[x * A.lanes + lane] : A.dim[x * A.lanes + lane];
+}
+
+__device__ __forceinline__ void add_stats(double* stats, int kind, double fl, double by) {
+    atomicAdd(&stats[kind], fl);
+    atomicAdd(&stats[H2_NKINDS + kind], by);
+}
+
+// scratch header (ints): [0] rk after recompression, [1] R', [2] r0, [3] t,
+// [4] recompression ran, [8 + ti] live rows of target ti
+constexpr int HDR_ROWS = 8;
+
+// ---- (i) recompression basis of row p (Sec. 3.4): one CTA per (cluster, lane)
+__global__ void __launch_bounds__(NT) k_recomp(FactorArgs A) {
     const int ci = blockIdx.x, lane = blockIdx.y;
     if (lane >= *A.active) return;
     __shared__ double red[32];
     __shared__ int redi[32];
-    __shared__ int s_neg, s_bad;
-    __shared__ double s_mp;
-    __shared__ int s_rk1;
+    __shared__ int s_bad;
     const int D = A.D, LN = A.lanes;
     const int p = A.cl[ci];
     const int m = A.dim[p * LN + lane], r0 = A.rk[p * LN + lane];
@@ -140,30 +158,20 @@ __global__ void __launch_bounds__(NT) k_factor(FactorArgs A) {
     double* colnorm = scr + A.lay.colnorm;
     double* Vr = scr + A.lay.vr;
     double* Vq = scr + A.lay.vq;
-    double* tmp = scr + A.lay.tmp;
-    double* F = scr + A.lay.f;
-    int* perm = (int*)(scr + A.lay.iperm);
-    int* piv = perm + D;
     int* hdr = (int*)(scr + A.lay.hdr);
-    int* hrows = hdr + 8;
-    double* Wb = scr + A.lay.w;
-    double* Yb = scr + A.lay.y;
-    auto live = [&](int x) {
-        return A.color[x] < A.cur_color ? A.rk[x * LN + lane] : A.dim[x * LN + lane];
-    };
-    if (threadIdx.x == 0) { s_neg = 0; s_bad = 0; s_mp = 1.0 / 0.0; s_rk1 = r0; }
-    __syncthreads();
-
-    // ---- (i) fill-in recompression of row p (Sec. 3.4) -------------------
     const int R = m - r0;
     const int nf = A.nfill[ci];
-    if (nf > 0 && R > 0) {
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    int t = 0;
+    const int run = (nf > 0 && R > 0) ? 1 : 0;
+    if (run) {
         int wz = 0;
-        for (int f = 0; f < nf; ++f) wz += live(A.fillq[ci * A.nfill_max + f]);
+        for (int f = 0; f < nf; ++f) wz += live_rows(A, A.fillq[ci * A.nfill_max + f], lane);
         int coff = 0;
         for (int f = 0; f < nf; ++f) {
             int q = A.fillq[ci * A.nfill_max + f];
-            int lq = live(q);
+            int lq = live_rows(A, q, lane);
             double* B = slot_ptr(A.slots, A.fillslot[ci * A.nfill_max + f], LN, lane, D);
             int tr = p > q ? 0 : 1;
             for (int e = threadIdx.x; e < R * lq; e += NT) {
@@ -174,152 +182,243 @@ __global__ void __launch_bounds__(NT) k_factor(FactorArgs A) {
         }
         __syncthreads();
         int capt = max(0, min(A.fill_cap, m) - r0);
-        int t = cta_pivqr<NT>(Z, wz, R, wz, A.tol, capt, Vr, D, colnorm, red, redi, &s_bad);
-        if (threadIdx.x == 0) {
-            double fl = 4.0 * R * (double)wz * t + 4.0 * (double)R * R * t;
-            double by = 8.0 * 2.0 * R * (double)wz;
-            if (t > 0) {
-                double sdx = 0.0;
-                for (int b = 0; b < A.nrow[ci]; ++b) sdx += A.dim[A.rowblk_other[ci * A.nrow_max + b] * LN + lane];
-                fl += 2.0 * R * (double)R * sdx + 2.0 * m * (double)R * R;
-                by += 8.0 * (2.0 * R * sdx + 2.0 * m * (double)R);
-            }
-            atomicAdd(&A.stats[H2_KIND_FACTOR], fl);
-            atomicAdd(&A.stats[H2_NKINDS + H2_KIND_FACTOR], by);
-        }
-        if (t > 0) {
-            cta_form_q<NT>(Vq, D, R, Vr, D, t);
-            const int nr = A.nrow[ci];
-            for (int b = 0; b < nr; ++b) {
-                int x = A.rowblk_other[ci * A.nrow_max + b];
-                int tr = A.rowblk_trans[ci * A.nrow_max + b];
-                double* B = slot_ptr(A.slots, A.rowblk[ci * A.nrow_max + b], LN, lane, D);
-                int dx = A.dim[x * LN + lane];
-                // rows r0.. of p: new = Vq^T old
-                for (int e = threadIdx.x; e < R * dx; e += NT) {
-                    int k = e / dx, j = e % dx;
-                    tmp[(size_t)k * D + j] = belem(B, D, tr, r0 + k, j);
-                }
-                __syncthreads();
-                for (int e = threadIdx.x; e < R * dx; e += NT) {
-                    int i = e / dx, j = e % dx;
-                    double v = 0.0;
-                    for (int k = 0; k < R; ++k) v += Vq[(size_t)k * D + i] * tmp[(size_t)k * D + j];
-                    belem(B, D, tr, r0 + i, j) = v;
-                }
-                __syncthreads();
-                if (x == p) {   // diagonal block: columns r0.. as well
-                    for (int e = threadIdx.x; e < m * R; e += NT) {
-                        int i = e / R, k = e % R;
-                        tmp[(size_t)i * D + k] = B[(size_t)i * D + r0 + k];
-                    }
-                    __syncthreads();
-                    for (int e = threadIdx.x; e < m * R; e += NT) {
-                        int i = e / R, j = e % R;
-                        double v = 0.0;
-                        for (int k = 0; k < R; ++k) v += tmp[(size_t)i * D + k] * Vq[(size_t)k * D + j];
-                        B[(size_t)i * D + r0 + j] = v;
-                    }
-                    __syncthreads();
-                }
-            }
-        }
-        // drop the remaining redundant rows of the fill-in blocks
-        for (int f = 0; f < nf; ++f) {
-            int q = A.fillq[ci * A.nfill_max + f];
-            int dq = A.dim[q * LN + lane];
-            double* B = slot_ptr(A.slots, A.fillslot[ci * A.nfill_max + f], LN, lane, D);
-            int tr = p > q ? 0 : 1;
-            int rows = m - (r0 + t);
-            for (int e = threadIdx.x; e < rows * dq; e += NT) {
-                int i = e / dq, j = e % dq;
-                belem(B, D, tr, r0 + t + i, j) = 0.0;
-            }
-        }
-        if (threadIdx.x == 0) {
-            s_rk1 = r0 + t;
-            A.rk[p * LN + lane] = r0 + t;
-        }
-        __syncthreads();
+        t = cta_pivqr<NT>(Z, wz, R, wz, A.tol, capt, Vr, D, colnorm, red, redi, &s_bad);
+        if (t > 0) cta_form_q<NT>(Vq, D, R, Vr, D, t);
+        if (threadIdx.x == 0)
+            add_stats(A.stats, H2_KIND_RECOMP, 4.0 * R * (double)wz * t + 4.0 * (double)R * R * t,
+                      8.0 * 2.0 * R * (double)wz);
     }
-    const int rk1 = s_rk1;
+    if (threadIdx.x == 0) {
+        hdr[2] = r0;
+        hdr[3] = t;
+        hdr[4] = run;
+        A.rk[p * LN + lane] = r0 + t;
+        if (s_bad) atomicOr(A.err, 1);
+    }
+}
+
+// ---- (ii) rotation of p's redundant coordinates in one block of row p and
+// truncation of a fill-in block: one CTA per (row block, cluster, lane)
+constexpr int RC = 32;   // column (or row) chunk staged in shared memory
+template <typename T>
+__global__ void __launch_bounds__(NT) k_rotate(FactorArgs A) {
+    const int ci = blockIdx.x / A.nrow_max, b = blockIdx.x % A.nrow_max, lane = blockIdx.y;
+    if (lane >= *A.active || b >= A.nrow[ci]) return;
+    extern __shared__ double tile[];          // R x RC
+    const int D = A.D, LN = A.lanes;
+    const int p = A.cl[ci];
+    const double* scr = A.scratch + ((size_t)ci * LN + lane) * A.lay.total;
+    const int* hdr = (const int*)(scr + A.lay.hdr);
+    if (!hdr[4]) return;
+    const int r0 = hdr[2], t = hdr[3];
+    const int m = A.dim[p * LN + lane];
+    const int R = m - r0;
+    const double* Vq = scr + A.lay.vq;
+    const int x = A.rowblk_other[ci * A.nrow_max + b];
+    const int tr = A.rowblk_trans[ci * A.nrow_max + b];
+    double* B = slot_ptr(A.slots, A.rowblk[ci * A.nrow_max + b], LN, lane, D);
+    double fl = 0.0;
+    if (t > 0) {
+        // rows r0.. of p: new = Vq^T old, over the live columns of x
+        const int dx = (x == p) ? m : live_rows(A, x, lane);
+        for (int j0 = 0; j0 < dx; j0 += RC) {
+            const int nj = min(RC, dx - j0);
+            for (int e = threadIdx.x; e < R * nj; e += NT) {
+                int k = e / nj, j = e % nj;
+                tile[k * RC + j] = belem(B, D, tr, r0 + k, j0 + j);
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < R * nj; e += NT) {
+                int i = e / nj, j = e % nj;
+                T v = 0;
+                for (int k = 0; k < R; ++k) v += (T)Vq[(size_t)k * D + i] * (T)tile[k * RC + j];
+                belem(B, D, tr, r0 + i, j0 + j) = (double)v;
+            }
+            __syncthreads();
+        }
+        fl += 2.0 * R * (double)R * dx;
+        if (x == p) {      // diagonal block: columns r0.. for every row
+            for (int i0 = 0; i0 < m; i0 += RC) {
+                const int ni = min(RC, m - i0);
+                for (int e = threadIdx.x; e < ni * R; e += NT) {
+                    int i = e / R, k = e % R;
+                    tile[k * RC + i] = B[(size_t)(i0 + i) * D + r0 + k];
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < ni * R; e += NT) {
+                    int i = e / R, j = e % R;
+                    T v = 0;
+                    for (int k = 0; k < R; ++k) v += (T)tile[k * RC + i] * (T)Vq[(size_t)k * D + j];
+                    B[(size_t)(i0 + i) * D + r0 + j] = (double)v;
+                }
+                __syncthreads();
+            }
+            fl += 2.0 * m * (double)R * R;
+        }
+    }
+    if (A.rowblk_fill[ci * A.nrow_max + b]) {   // drop the remaining redundant rows
+        const int dq = A.dim[x * LN + lane];
+        const int rows = m - (r0 + t);
+        for (int e = threadIdx.x; e < rows * dq; e += NT) {
+            int i = e / dq, j = e % dq;
+            belem(B, D, tr, r0 + t + i, j) = 0.0;
+        }
+    }
+    if (threadIdx.x == 0 && fl > 0.0) add_stats(A.stats, H2_KIND_ROTATE, fl, 8.0 * fl / R);
+}
+
+// ---- (iii) Bunch-Kaufman LDL^T of S_pp^RR (Eq. blr2-diag-ldl) and its
+// negative-pivot count: one CTA per (cluster, lane)
+template <int NTH>
+__global__ void __launch_bounds__(NTH) k_ldl(FactorArgs A, int use_smem) {
+    const int ci = blockIdx.x, lane = blockIdx.y;
+    if (lane >= *A.active) return;
+    extern __shared__ double sF[];
+    __shared__ double red[32];
+    __shared__ int redi[32];
+    __shared__ int s_neg, s_bad;
+    __shared__ double s_mp;
+    const int D = A.D, LN = A.lanes;
+    const int p = A.cl[ci];
+    const int m = A.dim[p * LN + lane], rk1 = A.rk[p * LN + lane];
     const int Rp = m - rk1;
+    double* scr = A.scratch + ((size_t)ci * LN + lane) * A.lay.total;
+    int* hdr = (int*)(scr + A.lay.hdr);
     if (threadIdx.x == 0) {
         hdr[0] = rk1;
         hdr[1] = Rp;
-        if (s_bad) atomicOr(A.err, 1);
+        s_neg = 0;
+        s_bad = 0;
+        s_mp = 1.0 / 0.0;
     }
     if (Rp <= 0) return;
-
-    // ---- (ii) Bunch-Kaufman LDL^T of S_pp^RR (Eq. blr2-diag-ldl) ------------
-    {
-        // the diagonal block is target 0 (a = p)
-        double* Bpp = slot_ptr(A.slots, A.targ_slot[ci * A.ntarg_max], LN, lane, D);
-        for (int e = threadIdx.x; e < Rp * Rp; e += NT) {
-            int i = e / Rp, j = e % Rp;
-            F[(size_t)i * D + j] = Bpp[(size_t)(rk1 + i) * D + rk1 + j];
-        }
-        __syncthreads();
-        cta_bk_ldl<NT>(F, D, Rp, perm, piv, red, redi, &s_neg, &s_mp, &s_bad, A.zero_pivot);
-        if (threadIdx.x == 0) {
-            atomicAdd(&A.neg[lane], (unsigned long long)s_neg);
-            double mp = s_mp;
-            if (!(mp >= 0.0)) mp = 0.0;
-            atomicMin(&A.minpiv[lane], (unsigned long long)__double_as_longlong(mp));
-            if (s_bad) atomicOr(A.err, 1);
-        }
-    }
-    // ---- (iii) W_a = S_ap^{.R} P L^{-T}, Y_a = W_a D^{-1} (Eq. blr2-diag-elimination)
-    const int nt = A.ntarg[ci];
-    for (int ti = threadIdx.x; ti < nt; ti += NT) {
-        int a = A.targ[ci * A.ntarg_max + ti];
-        hrows[ti] = (a == p) ? rk1 : live(a);
+    double* F = scr + A.lay.f;
+    int* perm = (int*)(scr + A.lay.iperm);
+    int* piv = perm + D;
+    const double* Bpp = slot_ptr(A.slots, A.targ_slot[ci * A.ntarg_max], LN, lane, D);   // target 0 = p
+    double* S = use_smem ? sF : F;
+    const int lds = use_smem ? Rp : D;
+    for (int e = threadIdx.x; e < Rp * Rp; e += NTH) {
+        int i = e / Rp, j = e % Rp;
+        S[(size_t)i * lds + j] = Bpp[(size_t)(rk1 + i) * D + rk1 + j];
     }
     __syncthreads();
-    int total_rows = 0;
-    for (int ti = 0; ti < nt; ++ti) total_rows += hrows[ti];
+    cta_bk_ldl<NTH>(S, lds, Rp, perm, piv, red, redi, &s_neg, &s_mp, &s_bad, A.zero_pivot);
+    if (use_smem)
+        for (int e = threadIdx.x; e < Rp * Rp; e += NTH) {
+            int i = e / Rp, j = e % Rp;
+            F[(size_t)i * D + j] = S[(size_t)i * lds + j];
+        }
     if (threadIdx.x == 0) {
-        double R3 = (double)Rp * Rp * Rp / 3.0;
-        double fl = R3 + (double)total_rows * Rp * Rp + (double)total_rows * Rp;
-        double by = 8.0 * ((double)Rp * Rp + 3.0 * (double)total_rows * Rp);
-        double fs = 0.0, bs = 0.0;
-        for (int i = 0; i < nt; ++i)
-            for (int j = 0; j <= i; ++j) {
-                double ra = hrows[i], rb = hrows[j];
-                fs += 2.0 * ra * rb * Rp;
-                bs += 8.0 * (ra * Rp + rb * Rp + 2.0 * ra * rb);
-            }
-        atomicAdd(&A.stats[H2_KIND_FACTOR], fl);
-        atomicAdd(&A.stats[H2_NKINDS + H2_KIND_FACTOR], by);
-        atomicAdd(&A.stats[H2_KIND_SCHUR], fs);
-        atomicAdd(&A.stats[H2_NKINDS + H2_KIND_SCHUR], bs);
+        atomicAdd(&A.neg[lane], (unsigned long long)s_neg);
+        double mp = s_mp;
+        if (!(mp >= 0.0)) mp = 0.0;
+        atomicMin(&A.minpiv[lane], (unsigned long long)__double_as_longlong(mp));
+        if (s_bad) atomicOr(A.err, 1);
+        add_stats(A.stats, H2_KIND_LDL, (double)Rp * Rp * Rp / 3.0, 16.0 * (double)Rp * Rp);
     }
-    for (int e = threadIdx.x; e < total_rows; e += NT) {
-        int ti = 0, i = e;
-        while (i >= hrows[ti]) { i -= hrows[ti]; ++ti; }
-        int tr = A.targ_trans[ci * A.ntarg_max + ti];
-        double* B = slot_ptr(A.slots, A.targ_slot[ci * A.ntarg_max + ti], LN, lane, D);
-        double* W = Wb + (size_t)ti * D * D + (size_t)i * D;
-        double* Y = Yb + (size_t)ti * D * D + (size_t)i * D;
-        for (int j = 0; j < Rp; ++j) {
-            double v = belem(B, D, tr, i, rk1 + perm[j]);
-            for (int k = 0; k < j; ++k) v -= W[k] * bk_L(F, D, piv, j, k);
-            W[j] = v;
+}
+
+// ---- (iv) W_a = S_ap^{.R} P L^{-T}, Y_a = W_a D^{-1} (Eq. blr2-diag-elimination):
+// one CTA per (target, cluster, lane); column-blocked forward substitution
+// (JB columns per block: a parallel update from the solved columns, then a
+// short per-row solve inside the block)
+constexpr int JB = 8;
+__global__ void __launch_bounds__(NT) k_trsm(FactorArgs A, int use_smem) {
+    const int ci = blockIdx.x / A.ntarg_max, ti = blockIdx.x % A.ntarg_max, lane = blockIdx.y;
+    if (lane >= *A.active || ti >= A.ntarg[ci]) return;
+    extern __shared__ double sh[];
+    const int D = A.D, LN = A.lanes;
+    const int p = A.cl[ci];
+    double* scr = A.scratch + ((size_t)ci * LN + lane) * A.lay.total;
+    int* hdr = (int*)(scr + A.lay.hdr);
+    const int rk1 = hdr[0], Rp = hdr[1];
+    if (Rp <= 0) return;
+    const int a = A.targ[ci * A.ntarg_max + ti];
+    const int rows = (a == p) ? rk1 : live_rows(A, a, lane);
+    if (threadIdx.x == 0) {
+        hdr[HDR_ROWS + ti] = rows;
+        double fs = 0.0, bs = 0.0;
+        for (int tj = 0; tj <= ti; ++tj) {
+            int b2 = A.targ[ci * A.ntarg_max + tj];
+            double rb = (b2 == p) ? rk1 : live_rows(A, b2, lane);
+            fs += 2.0 * rows * rb * Rp;
+            bs += 8.0 * (rows * (double)Rp + rb * Rp + 2.0 * rows * rb);
         }
-        for (int j = 0; j < Rp;) {
-            if (piv[j] == 1) {
-                Y[j] = W[j] / F[(size_t)j * D + j];
-                j += 1;
-            } else {
-                double a0 = F[(size_t)j * D + j], b0 = F[(size_t)(j + 1) * D + j],
-                       c0 = F[(size_t)(j + 1) * D + j + 1];
-                double det = a0 * c0 - b0 * b0;
-                double w0 = W[j], w1 = W[j + 1];
-                Y[j] = (w0 * c0 - w1 * b0) / det;
-                Y[j + 1] = (w1 * a0 - w0 * b0) / det;
-                j += 2;
+        add_stats(A.stats, H2_KIND_SCHUR, fs, bs);
+        add_stats(A.stats, H2_KIND_TRSM, (double)rows * Rp * Rp + (double)rows * Rp,
+                  8.0 * 3.0 * rows * (double)Rp);
+    }
+    if (rows <= 0) return;
+    // L, D and the pivots: staged in shared memory when they fit
+    const double* F = scr + A.lay.f;
+    const int* perm = (const int*)(scr + A.lay.iperm);
+    const int* piv = perm + D;
+    const double* sL = F;
+    int ldl = D;
+    const int* sperm = perm;
+    const int* spiv = piv;
+    if (use_smem) {
+        double* L2 = sh;                               // Rp x Rp
+        int* p2 = (int*)(sh + (size_t)Rp * Rp);
+        int* v2 = p2 + Rp;
+        for (int e = threadIdx.x; e < Rp * Rp; e += NT) L2[e] = F[(size_t)(e / Rp) * D + e % Rp];
+        for (int e = threadIdx.x; e < Rp; e += NT) { p2[e] = perm[e]; v2[e] = piv[e]; }
+        sL = L2;
+        ldl = Rp;
+        sperm = p2;
+        spiv = v2;
+    }
+    __syncthreads();
+    auto Lx = [&](int j, int k) {   // L(j, k), k < j, of the unit lower factor
+        return (spiv[k] == 2 && j == k + 1) ? 0.0 : sL[(size_t)j * ldl + k];
+    };
+    const int tr = A.targ_trans[ci * A.ntarg_max + ti];
+    const double* B = slot_ptr(A.slots, A.targ_slot[ci * A.ntarg_max + ti], LN, lane, D);
+    double* W = scr + A.lay.w + (size_t)ti * D * D;
+    double* Y = scr + A.lay.y + (size_t)ti * D * D;
+    for (int e = threadIdx.x; e < rows * Rp; e += NT) {       // W = S_ap^{.R} P
+        int i = e / Rp, j = e % Rp;
+        W[(size_t)i * D + j] = tr ? B[(size_t)(rk1 + sperm[j]) * D + i] : B[(size_t)i * D + rk1 + sperm[j]];
+    }
+    __syncthreads();
+    for (int jb = 0; jb < Rp; jb += JB) {
+        const int nb = min(JB, Rp - jb);
+        if (jb > 0) {
+            for (int e = threadIdx.x; e < rows * nb; e += NT) {
+                int i = e / nb, j = jb + e % nb;
+                double v = W[(size_t)i * D + j];
+                const double* wi = W + (size_t)i * D;
+                for (int k = 0; k < jb; ++k) v -= wi[k] * Lx(j, k);
+                W[(size_t)i * D + j] = v;
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < rows; i += NT) {
+            double* wi = W + (size_t)i * D;
+            for (int j = jb + 1; j < jb + nb; ++j) {
+                double v = wi[j];
+                for (int k = jb; k < j; ++k) v -= wi[k] * Lx(j, k);
+                wi[j] = v;
             }
         }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < rows * Rp; e += NT) {       // Y = W D^{-1}
+        int i = e / Rp, j = e % Rp;
+        const double* wi = W + (size_t)i * D;
+        double v;
+        if (spiv[j] == 1) {
+            v = wi[j] / sL[(size_t)j * ldl + j];
+        } else {
+            int j0 = spiv[j] == 2 ? j : j - 1;
+            double a0 = sL[(size_t)j0 * ldl + j0], b0 = sL[(size_t)(j0 + 1) * ldl + j0],
+                   c0 = sL[(size_t)(j0 + 1) * ldl + j0 + 1];
+            double det = a0 * c0 - b0 * b0;
+            double w0 = wi[j0], w1 = wi[j0 + 1];
+            v = (j == j0) ? (w0 * c0 - w1 * b0) / det : (w1 * a0 - w0 * b0) / det;
+        }
+        Y[(size_t)i * D + j] = v;
     }
 }
 
@@ -333,7 +432,10 @@ struct SchurArgs {
     const int* active;
 };
 
-// S_ab[i0:i0+32, j0:j0+32] -= W_a Y_b^T (Eq. blr2-diag-schur)
+// S_ab[i0:i0+32, j0:j0+32] -= W_a Y_b^T (Eq. blr2-diag-schur).  T is the
+// arithmetic of the products: double (FP64 path) or float (mixed path: FP32
+// products and accumulation, the FP64 block updated by the rounded result).
+template <typename T>
 __global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
     const int lane = blockIdx.y;
     if (lane >= *A.active) return;
@@ -344,24 +446,25 @@ __global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
     const int* hdr = (const int*)(scr + A.lay.hdr);
     const int Rp = hdr[1];
     if (Rp <= 0) return;
-    const int ra = hdr[8 + P.ta], rb = hdr[8 + P.tb];
+    const int ra = hdr[HDR_ROWS + P.ta], rb = hdr[HDR_ROWS + P.tb];
     const int i0 = (tile / A.tdim) * TS, j0 = (tile % A.tdim) * TS;
     if (i0 >= ra || j0 >= rb) return;
     const double* W = scr + A.lay.w + (size_t)P.ta * D * D;
     const double* Y = scr + A.lay.y + (size_t)P.tb * D * D;
-    __shared__ double sW[TS][TS + 1], sY[TS][TS + 1];
+    __shared__ T sW[TS][TS + 1], sY[TS][TS + 1];
     const int tx = threadIdx.x % TS, ty = threadIdx.x / TS;   // ty in 0..7
-    double acc[4] = {0, 0, 0, 0};
+    T acc[4] = {0, 0, 0, 0};
     for (int k0 = 0; k0 < Rp; k0 += TS) {
+        const int kc = min(TS, Rp - k0);
         for (int e = threadIdx.x; e < TS * TS; e += NT) {
             int r = e / TS, k = e % TS;
-            sW[r][k] = (i0 + r < ra && k0 + k < Rp) ? W[(size_t)(i0 + r) * D + k0 + k] : 0.0;
-            sY[r][k] = (j0 + r < rb && k0 + k < Rp) ? Y[(size_t)(j0 + r) * D + k0 + k] : 0.0;
+            sW[r][k] = (i0 + r < ra && k < kc) ? (T)W[(size_t)(i0 + r) * D + k0 + k] : (T)0;
+            sY[r][k] = (j0 + r < rb && k < kc) ? (T)Y[(size_t)(j0 + r) * D + k0 + k] : (T)0;
         }
         __syncthreads();
 #pragma unroll 8
-        for (int k = 0; k < TS; ++k) {
-            double y = sY[tx][k];
+        for (int k = 0; k < kc; ++k) {
+            T y = sY[tx][k];
 #pragma unroll
             for (int u = 0; u < 4; ++u) acc[u] += sW[ty + 8 * u][k] * y;
         }
@@ -371,7 +474,7 @@ __global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         int i = i0 + ty + 8 * u, j = j0 + tx;
-        if (i < ra && j < rb) belem(B, D, P.trans, i, j) -= acc[u];
+        if (i < ra && j < rb) belem(B, D, P.trans, i, j) -= (double)acc[u];
     }
 }
 
@@ -571,10 +674,12 @@ __global__ void k_finish(const unsigned long long* neg, const unsigned long long
 }
 
 // ------------------------------------------------------------ workspace --
+constexpr size_t kSmemCap = 200 * 1024;   // dynamic shared memory staged per CTA at most
+
 struct ColourDev {
-    int ncl, ntarg_max, nrow_max, nfill_max, npairs;
-    int *cl, *targ, *targ_slot, *targ_trans, *ntarg, *rowblk, *rowblk_other, *rowblk_trans, *nrow,
-        *fillq, *fillslot, *nfill;
+    int ncl, ntarg_max, nrow_max, nfill_max, npairs, has_fill;
+    int *cl, *targ, *targ_slot, *targ_trans, *ntarg, *rowblk, *rowblk_other, *rowblk_trans, *rowblk_fill,
+        *nrow, *fillq, *fillslot, *nfill;
     SchurPair* pairs;
 };
 
@@ -648,13 +753,15 @@ int alloc_workspace(h2_matrix* h, int lanes) {
         // colour work lists
         for (const auto& cl : lp.color_lists) {
             ColourDev C{};
+            C.has_fill = 0;
             C.ncl = (int)cl.size();
             C.ntarg_max = ntarg_max;
             C.nrow_max = nrow_max;
             C.nfill_max = nfill_max;
             std::vector<int> targ(C.ncl * ntarg_max, -1), tslot(C.ncl * ntarg_max, -1),
                 ttr(C.ncl * ntarg_max, 0), ntarg(C.ncl), rowblk(C.ncl * nrow_max, -1),
-                rowother(C.ncl * nrow_max, -1), rowtr(C.ncl * nrow_max, 0), nrow(C.ncl),
+                rowother(C.ncl * nrow_max, -1), rowtr(C.ncl * nrow_max, 0), rowfill(C.ncl * nrow_max, 0),
+                nrow(C.ncl),
                 fillq(C.ncl * nfill_max, -1), fillslot(C.ncl * nfill_max, -1), nfill(C.ncl);
             std::vector<SchurPair> pairs;
             auto slot = [&](int a, int b) { return D.slot_of[(size_t)std::max(a, b) * nc + std::min(a, b)]; };
@@ -681,6 +788,7 @@ int alloc_workspace(h2_matrix* h, int lanes) {
                         rowblk[ci * nrow_max + nr] = slot(p, x);
                         rowother[ci * nrow_max + nr] = x;
                         rowtr[ci * nrow_max + nr] = x > p ? 1 : 0;
+                        rowfill[ci * nrow_max + nr] = lp.is_fill(p, x) ? 1 : 0;
                         ++nr;
                     }
                     if (lp.is_fill(p, x)) {
@@ -691,12 +799,14 @@ int alloc_workspace(h2_matrix* h, int lanes) {
                 }
                 nrow[ci] = nr;
                 nfill[ci] = nfl;
+                if (nfl > 0) C.has_fill = 1;
             }
             C.npairs = (int)pairs.size();
             if ((rc = upload(&C.cl, std::vector<int>(cl.begin(), cl.end()))) || (rc = upload(&C.targ, targ)) ||
                 (rc = upload(&C.targ_slot, tslot)) || (rc = upload(&C.targ_trans, ttr)) ||
                 (rc = upload(&C.ntarg, ntarg)) || (rc = upload(&C.rowblk, rowblk)) ||
                 (rc = upload(&C.rowblk_other, rowother)) || (rc = upload(&C.rowblk_trans, rowtr)) ||
+                (rc = upload(&C.rowblk_fill, rowfill)) ||
                 (rc = upload(&C.nrow, nrow)) || (rc = upload(&C.fillq, fillq)) ||
                 (rc = upload(&C.fillslot, fillslot)) || (rc = upload(&C.nfill, nfill)) ||
                 (rc = upload(&C.pairs, pairs)))
@@ -705,6 +815,11 @@ int alloc_workspace(h2_matrix* h, int lanes) {
         }
         if ((rc = upload(&W.d_slot_of, D.slot_of)) || (rc = upload(&W.d_far_of, D.far_of))) return rc;
     }
+    CK(cudaFuncSetAttribute(k_rotate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_rotate<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_ldl<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_ldl<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
     // buffers
     ws.d_slots.assign(L + 1, nullptr);
     ws.d_dim.assign(L + 1, nullptr);
@@ -752,7 +867,7 @@ struct Profiler {
 
 // enqueue one full factorization of the workspace's lanes on stream st;
 // returns the number of kernel launches
-static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof = nullptr) {
+static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, int mixed) {
     const Plan& P = h->plan;
     const int L = P.L;
     Workspace& ws = h->ws;
@@ -781,17 +896,42 @@ static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof =
             const ColourDev& C = W.colours[c];
             FactorArgs fa{ws.d_slots[l], D.dmax, LN, ws.d_dim[l], ws.d_rk[l], D.d_color, c, C.cl, C.targ,
                           C.targ_slot, C.targ_trans, C.ntarg, C.ntarg_max, C.rowblk, C.rowblk_other,
-                          C.rowblk_trans, C.nrow, C.nrow_max, C.fillq, C.fillslot, C.nfill, C.nfill_max,
-                          ws.d_scratch, W.lay, h->tol, 2.220446049250313e-16 * h->norm_inf,
+                          C.rowblk_trans, C.rowblk_fill, C.nrow, C.nrow_max, C.fillq, C.fillslot, C.nfill,
+                          C.nfill_max, ws.d_scratch, W.lay, h->tol, 2.220446049250313e-16 * h->norm_inf,
                           h->fill_cap_eff, ws.d_neg, ws.d_minpiv, ws.d_err, fs->d_active, fs->d_stats};
-            B(H2_KIND_FACTOR);
-            k_factor<<<dim3(C.ncl, LN), NT, 0, st>>>(fa);
+            const int Dm = D.dmax;
+            if (C.has_fill) {
+                B(H2_KIND_RECOMP);
+                k_recomp<<<dim3(C.ncl, LN), NT, 0, st>>>(fa);
+                E();
+                B(H2_KIND_ROTATE);
+                if (mixed)
+                    k_rotate<float><<<dim3(C.ncl * C.nrow_max, LN), NT, (size_t)Dm * RC * sizeof(double), st>>>(fa);
+                else
+                    k_rotate<double><<<dim3(C.ncl * C.nrow_max, LN), NT, (size_t)Dm * RC * sizeof(double), st>>>(fa);
+                E();
+            }
+            const size_t sm_ldl = (size_t)Dm * Dm * sizeof(double);
+            const int ldl_smem = sm_ldl <= kSmemCap ? 1 : 0;
+            B(H2_KIND_LDL);
+            if (Dm <= 64)
+                k_ldl<128><<<dim3(C.ncl, LN), 128, ldl_smem ? sm_ldl : 0, st>>>(fa, ldl_smem);
+            else
+                k_ldl<NT><<<dim3(C.ncl, LN), NT, ldl_smem ? sm_ldl : 0, st>>>(fa, ldl_smem);
+            E();
+            const size_t sm_trsm = (size_t)Dm * Dm * sizeof(double) + 2 * (size_t)Dm * sizeof(int);
+            const int trsm_smem = sm_trsm <= kSmemCap ? 1 : 0;
+            B(H2_KIND_TRSM);
+            k_trsm<<<dim3(C.ncl * C.ntarg_max, LN), NT, trsm_smem ? sm_trsm : 0, st>>>(fa, trsm_smem);
             E();
             int tdim = (D.dmax + TS - 1) / TS;
             SchurArgs sa{ws.d_slots[l], D.dmax, LN, C.pairs, tdim * tdim, tdim, ws.d_scratch, W.lay,
                          fs->d_active};
             B(H2_KIND_SCHUR);
-            k_schur<<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
+            if (mixed)
+                k_schur<float><<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
+            else
+                k_schur<double><<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
             E();
         }
         if (l > 0) {
@@ -816,16 +956,25 @@ static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof =
     return nl;
 }
 
-static int ensure_graph(h2_matrix* h) {
+static int ensure_graph(h2_matrix* h, int mixed) {
     Workspace& ws = h->ws;
-    if (ws.graph) return H2_OK;
+    cudaGraphExec_t& ge = mixed ? ws.graph_mixed : ws.graph;
+    if (ge) return H2_OK;
     cudaStream_t st = h->stream;
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    h->kernels_per_batch = enqueue_factorization(h, st);
+    h->kernels_per_batch = enqueue_factorization(h, st, nullptr, mixed);
     CK(cudaStreamEndCapture(st, &g));
-    CK(cudaGraphInstantiate(&ws.graph, g, 0));
+    CK(cudaGraphInstantiate(&ge, g, 0));
     cudaGraphDestroy(g);
+    return H2_OK;
+}
+
+// launch one batch of the lanes already in ws.d_shifts (count set on device)
+static int launch_batch(h2_matrix* h, int mixed) {
+    int rc = ensure_graph(h, mixed);
+    if (rc) return rc;
+    CK(cudaGraphLaunch(mixed ? h->ws.graph_mixed : h->ws.graph, h->stream));
     return H2_OK;
 }
 
@@ -838,13 +987,57 @@ int run_inertia(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts,
         set_error("h2_inertia_device: ns exceeds max_lanes");
         return H2_ERR_INVALID_ARG;
     }
-    int rc = ensure_graph(h);
+    int rc = ensure_graph(h, h->opt.precision == H2_PREC_MIXED);
     if (rc) return rc;
     CK(cudaMemcpyAsync(ws.d_shifts, d_shifts, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
     k_set_int<<<1, 1, 0, st>>>(fs->d_active, ns);
-    CK(cudaGraphLaunch(ws.graph, st));
+    if ((rc = launch_batch(h, h->opt.precision == H2_PREC_MIXED))) return rc;
     CK(cudaMemcpyAsync(d_counts, fs->d_counts, ns * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
     if (d_minpiv) CK(cudaMemcpyAsync(d_minpiv, fs->d_mp, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return H2_OK;
+}
+
+// one batch of host shifts (nb <= lanes) in the given precision; counts and
+// min |pivot| back to host arrays
+static int host_batch(h2_matrix* h, const double* shifts, int nb, int mixed, int64_t* counts, double* minpiv) {
+    Workspace& ws = h->ws;
+    FactorState* fs = state_of(h);
+    cudaStream_t st = h->stream;
+    CK(cudaMemcpyAsync(ws.d_shifts, shifts, nb * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_set_int<<<1, 1, 0, st>>>(fs->d_active, nb);
+    int rc = launch_batch(h, mixed);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(counts, fs->d_counts, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(minpiv, fs->d_mp, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, ws.d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err) {
+        set_error("NaN pivot in the factorization");
+        return H2_ERR_NUMERICAL;
+    }
+    return H2_OK;
+}
+
+// mixed precision guard: shifts of the batch whose min |pivot| is below
+// pivot_guard * ||A||_inf are factorized again in FP64 (counts and pivots
+// replaced).  Returns the number of shifts re-run.
+static int guard_rerun(h2_matrix* h, const double* shifts, int nb, int64_t* counts, double* minpiv, int* rerun) {
+    const double theta = h->opt.pivot_guard * h->norm_inf;
+    std::vector<int> idx;
+    for (int i = 0; i < nb; ++i)
+        if (!(minpiv[i] >= theta)) idx.push_back(i);
+    *rerun = (int)idx.size();
+    if (idx.empty()) return H2_OK;
+    std::vector<double> s2(idx.size()), m2(idx.size());
+    std::vector<int64_t> c2(idx.size());
+    for (size_t j = 0; j < idx.size(); ++j) s2[j] = shifts[idx[j]];
+    int rc = host_batch(h, s2.data(), (int)idx.size(), 0, c2.data(), m2.data());
+    if (rc) return rc;
+    for (size_t j = 0; j < idx.size(); ++j) {
+        counts[idx[j]] = c2[j];
+        minpiv[idx[j]] = m2[j];
+    }
     return H2_OK;
 }
 
@@ -861,7 +1054,7 @@ int run_profile(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts,
     k_set_int<<<1, 1, 0, st>>>(fs->d_active, ns);
     Profiler pr;
     pr.st = st;
-    int nl = enqueue_factorization(h, st, &pr);
+    int nl = enqueue_factorization(h, st, &pr, h->opt.precision == H2_PREC_MIXED);
     CK(cudaMemcpyAsync(d_counts, fs->d_counts, ns * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
     double stats[2 * H2_NKINDS];
     CK(cudaMemcpyAsync(stats, fs->d_stats, sizeof(stats), cudaMemcpyDeviceToHost, st));
@@ -884,28 +1077,25 @@ int run_profile(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts,
 }
 
 // host arrays: each batch of <= lanes shifts is copied in, factorized and its
-// counts copied back (the end-to-end path of h2_inertia)
+// counts copied back (the end-to-end path of h2_inertia); in mixed precision
+// the guarded shifts of each batch are re-run in FP64
 int run_inertia_host(h2_matrix* h, const double* shifts, int64_t ns, int64_t* counts, double* minpiv) {
     Workspace& ws = h->ws;
-    FactorState* fs = state_of(h);
     cudaStream_t st = h->stream;
-    int rc = ensure_graph(h);
-    if (rc) return rc;
+    const int mixed = h->opt.precision == H2_PREC_MIXED;
     CK(cudaMemsetAsync(ws.d_err, 0, sizeof(int), st));
+    std::vector<double> mp(ws.lanes);
+    h->last_guarded = 0;
     for (int64_t b0 = 0; b0 < ns; b0 += ws.lanes) {
         int nb = (int)std::min<int64_t>(ws.lanes, ns - b0);
-        CK(cudaMemcpyAsync(ws.d_shifts, shifts + b0, nb * sizeof(double), cudaMemcpyHostToDevice, st));
-        k_set_int<<<1, 1, 0, st>>>(fs->d_active, nb);
-        CK(cudaGraphLaunch(ws.graph, st));
-        CK(cudaMemcpyAsync(counts + b0, fs->d_counts, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        if (minpiv) CK(cudaMemcpyAsync(minpiv + b0, fs->d_mp, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-        int err = 0;
-        CK(cudaMemcpyAsync(&err, ws.d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (err) {
-            set_error("h2_inertia: NaN pivot in the factorization");
-            return H2_ERR_NUMERICAL;
+        int rc = host_batch(h, shifts + b0, nb, mixed, counts + b0, mp.data());
+        if (rc) return rc;
+        if (mixed) {
+            int nre = 0;
+            if ((rc = guard_rerun(h, shifts + b0, nb, counts + b0, mp.data(), &nre))) return rc;
+            h->last_guarded += nre;
         }
+        if (minpiv) std::memcpy(minpiv + b0, mp.data(), nb * sizeof(double));
     }
     return H2_OK;
 }
@@ -962,28 +1152,64 @@ __global__ void k_bisect_update(double* lo, double* hi, const int64_t* kk, int n
     hi[k] = b;
 }
 
+// One multisection round on the device-resident intervals: plan the shifts of
+// the distinct intervals wider than `width`, factorize them in the given
+// precision (mixed with guard: low-pivot shifts re-run in FP64) and narrow
+// every k.  h2_kth_eig runs its mixed rounds unguarded: a wrong mixed count
+// at mu implies |lambda_k - mu| < ||E|| << Delta, so the FP64 check of the
+// widened bracket certifies the result.
+// Returns the number of active intervals (0: nothing to do) in *nact.
+static int kth_round(h2_matrix* h, int nk, double width, int mixed, int guard, int* nact) {
+    Workspace& ws = h->ws;
+    FactorState* fs = state_of(h);
+    cudaStream_t st = h->stream;
+    k_bisect_plan<<<1, 32, 0, st>>>(fs->d_lo, fs->d_hi, nk, width, ws.lanes, ws.d_shifts, fs->d_active, fs->d_nact);
+    int used = 0;
+    CK(cudaMemcpyAsync(nact, fs->d_nact, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&used, fs->d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (*nact == 0) return H2_OK;
+    int rc = launch_batch(h, mixed);
+    if (rc) return rc;
+    if (mixed && guard) {
+        std::vector<double> sh(used), mp(used);
+        std::vector<int64_t> cnt(used);
+        CK(cudaMemcpyAsync(sh.data(), ws.d_shifts, used * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(cnt.data(), fs->d_counts, used * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(mp.data(), fs->d_mp, used * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        int nre = 0;
+        if ((rc = guard_rerun(h, sh.data(), used, cnt.data(), mp.data(), &nre))) return rc;
+        h->last_guarded += nre;
+        if (nre) {   // restore the round's shifts and the corrected counts
+            CK(cudaMemcpyAsync(ws.d_shifts, sh.data(), used * sizeof(double), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(fs->d_counts, cnt.data(), used * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+            k_set_int<<<1, 1, 0, st>>>(fs->d_active, used);
+        }
+    }
+    k_bisect_update<<<(unsigned)((nk + 127) / 128), 128, 0, st>>>(fs->d_lo, fs->d_hi, fs->d_k, nk, ws.d_shifts,
+                                                                 fs->d_counts, fs->d_active);
+    h->last_shifts += used;
+    return H2_OK;
+}
+
 int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out, double* err_bound) {
     Workspace& ws = h->ws;
     FactorState* fs = state_of(h);
     cudaStream_t st = h->stream;
-    int rc = ensure_graph(h);
-    if (rc) return rc;
+    int rc;
     if (nk > 1024) {
         set_error("h2_kth_eig: at most 1024 k per call");
         return H2_ERR_INVALID_ARG;
     }
-    // start interval: Gershgorin padded by 1e-6 ||A||_inf; check nu(a) = 0, nu(b) = n
-    double a = h->glo - 1e-6 * h->norm_inf, b = h->ghi + 1e-6 * h->norm_inf;
-    {
-        double sh[2] = {a, b};
-        int two = std::min(2, ws.lanes);
-        CK(cudaMemcpyAsync(ws.d_shifts, sh, two * sizeof(double), cudaMemcpyHostToDevice, st));
-        k_set_int<<<1, 1, 0, st>>>(fs->d_active, two);
-        CK(cudaGraphLaunch(ws.graph, st));
+    CK(cudaMemsetAsync(ws.d_err, 0, sizeof(int), st));
+    // start interval: Gershgorin padded by 1e-6 ||A||_inf; check nu(a) = 0, nu(b) = n in FP64
+    const double a = h->glo - 1e-6 * h->norm_inf, b = h->ghi + 1e-6 * h->norm_inf;
+    if (ws.lanes >= 2) {
+        double sh[2] = {a, b}, mp[2];
         int64_t cnt[2] = {0, 0};
-        CK(cudaMemcpyAsync(cnt, fs->d_counts, two * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (two == 2 && (cnt[0] != 0 || cnt[1] != h->n)) {
+        if ((rc = host_batch(h, sh, 2, 0, cnt, mp))) return rc;
+        if (cnt[0] != 0 || cnt[1] != h->n) {
             set_error("h2_kth_eig: nu(a) != 0 or nu(b) != n on the Gershgorin interval");
             return H2_ERR_INTERVAL;
         }
@@ -999,26 +1225,64 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
     CK(cudaMemcpyAsync(fs->d_lo, lo.data(), nk * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(fs->d_hi, hi.data(), nk * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(fs->d_k, k, nk * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    int rounds = 0;
+    int rounds = 0, nact = 0;
     h->last_rounds = 0;
     h->last_shifts = 0;
-    while (true) {
-        k_bisect_plan<<<1, 32, 0, st>>>(fs->d_lo, fs->d_hi, (int)nk, tol, ws.lanes, ws.d_shifts, fs->d_active,
-                                        fs->d_nact);
-        int nact = 0, used = 0;
-        CK(cudaMemcpyAsync(&nact, fs->d_nact, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(&used, fs->d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (nact == 0) break;
-        CK(cudaGraphLaunch(ws.graph, st));
-        k_bisect_update<<<(unsigned)((nk + 127) / 128), 128, 0, st>>>(fs->d_lo, fs->d_hi, fs->d_k, (int)nk,
-                                                                     ws.d_shifts, fs->d_counts, fs->d_active);
-        ++rounds;
-        h->last_shifts += used;
-        if (rounds > 4096) {
-            set_error("h2_kth_eig: bisection did not converge");
-            return H2_ERR_NUMERICAL;
+    h->last_guarded = 0;
+    h->last_mixed_rounds = 0;
+    if (h->opt.precision == H2_PREC_MIXED) {
+        // mixed rounds while the brackets are wider than Delta = 64 u_32 ||A||_inf
+        const double delta = 64.0 * 0x1.0p-24 * h->norm_inf;
+        while (true) {
+            if ((rc = kth_round(h, (int)nk, std::max(tol, delta), 1, 0, &nact))) return rc;
+            if (nact == 0) break;
+            ++rounds;
+            ++h->last_mixed_rounds;
+            if (rounds > 4096) { set_error("h2_kth_eig: no convergence"); return H2_ERR_NUMERICAL; }
         }
+        // widen every bracket by Delta and verify it in FP64: nu(lo) < k <= nu(hi);
+        // a bracket that fails restarts from the Gershgorin interval
+        CK(cudaMemcpyAsync(lo.data(), fs->d_lo, nk * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hi.data(), fs->d_hi, nk * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<double> pts;
+        for (int64_t i = 0; i < nk; ++i) {
+            lo[i] = std::max(a, lo[i] - delta);
+            hi[i] = std::min(b, hi[i] + delta);
+            pts.push_back(lo[i]);
+            pts.push_back(hi[i]);
+        }
+        std::sort(pts.begin(), pts.end());
+        pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
+        std::vector<int64_t> cnt(pts.size());
+        std::vector<double> mp(pts.size());
+        for (size_t b0 = 0; b0 < pts.size(); b0 += ws.lanes) {
+            int nb = (int)std::min<size_t>(ws.lanes, pts.size() - b0);
+            if ((rc = host_batch(h, pts.data() + b0, nb, 0, cnt.data() + b0, mp.data() + b0))) return rc;
+        }
+        h->last_shifts += (int64_t)pts.size();
+        auto count_at = [&](double x) {
+            size_t j = std::lower_bound(pts.begin(), pts.end(), x) - pts.begin();
+            return cnt[j];
+        };
+        for (int64_t i = 0; i < nk; ++i) {
+            int64_t cl = (lo[i] == a) ? 0 : count_at(lo[i]);
+            int64_t ch = (hi[i] == b) ? h->n : count_at(hi[i]);
+            if (!(cl < k[i] && k[i] <= ch)) {
+                lo[i] = a;
+                hi[i] = b;
+                ++h->last_bracket_resets;
+            }
+        }
+        CK(cudaMemcpyAsync(fs->d_lo, lo.data(), nk * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(fs->d_hi, hi.data(), nk * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    // FP64 rounds to the requested width (Algorithm 1's stopping rule)
+    while (true) {
+        if ((rc = kth_round(h, (int)nk, tol, 0, 0, &nact))) return rc;
+        if (nact == 0) break;
+        ++rounds;
+        if (rounds > 4096) { set_error("h2_kth_eig: bisection did not converge"); return H2_ERR_NUMERICAL; }
     }
     h->last_rounds = rounds;
     CK(cudaMemcpyAsync(lo.data(), fs->d_lo, nk * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1040,7 +1304,9 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
 void free_workspace(h2_matrix* h) {
     Workspace& ws = h->ws;
     if (ws.graph) cudaGraphExecDestroy(ws.graph);
+    if (ws.graph_mixed) cudaGraphExecDestroy(ws.graph_mixed);
     ws.graph = nullptr;
+    ws.graph_mixed = nullptr;
     for (auto p : ws.d_slots) cudaFree(p);
     for (auto p : ws.d_dim) cudaFree(p);
     for (auto p : ws.d_rk) cudaFree(p);
@@ -1052,6 +1318,7 @@ void free_workspace(h2_matrix* h) {
             for (auto& C : W.colours) {
                 cudaFree(C.cl); cudaFree(C.targ); cudaFree(C.targ_slot); cudaFree(C.targ_trans);
                 cudaFree(C.ntarg); cudaFree(C.rowblk); cudaFree(C.rowblk_other); cudaFree(C.rowblk_trans);
+                cudaFree(C.rowblk_fill);
                 cudaFree(C.nrow); cudaFree(C.fillq); cudaFree(C.fillslot); cudaFree(C.nfill); cudaFree(C.pairs);
             }
             cudaFree(W.d_slot_of); cudaFree(W.d_far_of);

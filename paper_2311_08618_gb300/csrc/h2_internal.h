@@ -111,7 +111,8 @@ struct Workspace {
     int* d_err = nullptr;          // error flags
     double* d_shifts = nullptr;    // [lanes]
     size_t bytes = 0;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;        // FP64 batch
+    cudaGraphExec_t graph_mixed = nullptr;  // mixed-precision batch
     void* graph_state = nullptr;   // factorization work lists (h2_factor.cu)
 };
 
@@ -139,6 +140,9 @@ struct h2_matrix {
     int last_rounds = 0;           // bisection rounds of the last h2_kth_eig
     int64_t last_shifts = 0;       // shifts evaluated by the last h2_kth_eig
     int kernels_per_batch = 0;     // launches in one batch (graph nodes)
+    int64_t last_guarded = 0;      // mixed precision: shifts re-run in FP64 by the last call
+    int last_mixed_rounds = 0;     // mixed rounds of the last h2_kth_eig
+    int64_t last_bracket_resets = 0;  // brackets that failed the FP64 verification
 };
 
 namespace h2 {
