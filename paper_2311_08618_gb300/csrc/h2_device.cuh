@@ -208,10 +208,18 @@ __device__ void cta_form_q(double* Q, int ldq, int m, const double* V, int ldv, 
 // original index of position j, and piv[j] = 1 (1x1), 2 (first of a 2x2),
 // 0 (second of a 2x2).  Accumulates #negative eigenvalues of D into *neg and
 // the smallest |eigenvalue| of a D block into *minpiv (thread 0's values).
+// buf: 4n doubles (shared memory preferred): the pivot column(s) and the
+// multipliers of the current step, so that the trailing update divides once
+// per row (l_i = c_i / d) and then only multiplies (S_ij -= l_i c_j).
 template <int NT>
 __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, double* red,
-                           int* redi, int* neg, double* minpiv, int* bad, double zero_pivot) {
+                           int* redi, int* neg, double* minpiv, int* bad, double zero_pivot,
+                           double* buf) {
     const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+    double* c0 = buf;
+    double* c1 = buf + n;
+    double* l0 = buf + 2 * n;
+    double* l1 = buf + 3 * n;
     for (int i = threadIdx.x; i < n; i += NT) perm[i] = i;
     __syncthreads();
     int k = 0;
@@ -289,14 +297,19 @@ __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, doubl
                 if (d != d) *bad = 1;
             }
             if (d != 0.0 && k + 1 < n) {
-                // l = S[k+1:, k] / d ; S[k+1:, k+1:] -= l * S[k+1:, k]^T
+                // c = S[k+1:, k], l = c / d ; S[k+1:, k+1:] -= l c^T ; S[k+1:, k] = l
+                for (int i = k + 1 + threadIdx.x; i < n; i += NT) {
+                    double c = S[(size_t)i * lds + k];
+                    c0[i] = c;
+                    l0[i] = c / d;
+                }
+                __syncthreads();
                 int t = n - k - 1;
                 for (int e = threadIdx.x; e < t * t; e += NT) {
                     int i = k + 1 + e / t, j = k + 1 + e % t;
-                    S[(size_t)i * lds + j] -= (S[(size_t)i * lds + k] / d) * S[(size_t)j * lds + k];
+                    S[(size_t)i * lds + j] -= l0[i] * c0[j];
                 }
-                __syncthreads();
-                for (int i = k + 1 + threadIdx.x; i < n; i += NT) S[(size_t)i * lds + k] /= d;
+                for (int i = k + 1 + threadIdx.x; i < n; i += NT) S[(size_t)i * lds + k] = l0[i];
             }
             __syncthreads();
             k += 1;
@@ -317,18 +330,22 @@ __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, doubl
             if (k + 2 < n) {
                 // Lc = C E^{-1}; S[k+2:, k+2:] -= Lc C^T ; store Lc in S[k+2:, k:k+2]
                 double i00 = c / det, i01 = -b / det, i11 = a / det;
+                for (int i = k + 2 + threadIdx.x; i < n; i += NT) {
+                    double ci0 = S[(size_t)i * lds + k], ci1 = S[(size_t)i * lds + k + 1];
+                    c0[i] = ci0;
+                    c1[i] = ci1;
+                    l0[i] = ci0 * i00 + ci1 * i01;
+                    l1[i] = ci0 * i01 + ci1 * i11;
+                }
+                __syncthreads();
                 int t = n - k - 2;
                 for (int e = threadIdx.x; e < t * t; e += NT) {
                     int i = k + 2 + e / t, j = k + 2 + e % t;
-                    double ci0 = S[(size_t)i * lds + k], ci1 = S[(size_t)i * lds + k + 1];
-                    double l0 = ci0 * i00 + ci1 * i01, l1 = ci0 * i01 + ci1 * i11;
-                    S[(size_t)i * lds + j] -= l0 * S[(size_t)j * lds + k] + l1 * S[(size_t)j * lds + k + 1];
+                    S[(size_t)i * lds + j] -= l0[i] * c0[j] + l1[i] * c1[j];
                 }
-                __syncthreads();
                 for (int i = k + 2 + threadIdx.x; i < n; i += NT) {
-                    double ci0 = S[(size_t)i * lds + k], ci1 = S[(size_t)i * lds + k + 1];
-                    S[(size_t)i * lds + k] = ci0 * i00 + ci1 * i01;
-                    S[(size_t)i * lds + k + 1] = ci0 * i01 + ci1 * i11;
+                    S[(size_t)i * lds + k] = l0[i];
+                    S[(size_t)i * lds + k + 1] = l1[i];
                 }
             }
             __syncthreads();

@@ -298,12 +298,13 @@ __global__ void __launch_bounds__(NTH) k_ldl(FactorArgs A, int use_smem) {
     const double* Bpp = slot_ptr(A.slots, A.targ_slot[ci * A.ntarg_max], LN, lane, D);   // target 0 = p
     double* S = use_smem ? sF : F;
     const int lds = use_smem ? Rp : D;
+    double* bkbuf = use_smem ? sF + (size_t)Rp * Rp : scr + A.lay.tmp;   // 4 Rp <= D*D doubles
     for (int e = threadIdx.x; e < Rp * Rp; e += NTH) {
         int i = e / Rp, j = e % Rp;
         S[(size_t)i * lds + j] = Bpp[(size_t)(rk1 + i) * D + rk1 + j];
     }
     __syncthreads();
-    cta_bk_ldl<NTH>(S, lds, Rp, perm, piv, red, redi, &s_neg, &s_mp, &s_bad, A.zero_pivot);
+    cta_bk_ldl<NTH>(S, lds, Rp, perm, piv, red, redi, &s_neg, &s_mp, &s_bad, A.zero_pivot, bkbuf);
     if (use_smem)
         for (int e = threadIdx.x; e < Rp * Rp; e += NTH) {
             int i = e / Rp, j = e % Rp;
@@ -911,7 +912,7 @@ static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, 
                     k_rotate<double><<<dim3(C.ncl * C.nrow_max, LN), NT, (size_t)Dm * RC * sizeof(double), st>>>(fa);
                 E();
             }
-            const size_t sm_ldl = (size_t)Dm * Dm * sizeof(double);
+            const size_t sm_ldl = ((size_t)Dm * Dm + 4 * (size_t)Dm) * sizeof(double);
             const int ldl_smem = sm_ldl <= kSmemCap ? 1 : 0;
             B(H2_KIND_LDL);
             if (Dm <= 64)

@@ -25,9 +25,10 @@ constexpr int NT = 256;
 __global__ void __launch_bounds__(NT) k_dense_inertia(const double* __restrict__ A, int n, int lda,
                                                      const double* __restrict__ shifts, int64_t* counts,
                                                      double* minpiv, double* scratch) {
-    extern __shared__ int sh_int[];
-    int* perm = sh_int;
-    int* piv = sh_int + n;
+    extern __shared__ double sh_dbl[];
+    double* bkbuf = sh_dbl;                       // 4n doubles
+    int* perm = (int*)(sh_dbl + 4 * n);
+    int* piv = perm + n;
     __shared__ double red[32];
     __shared__ int redi[32];
     __shared__ int s_neg, s_bad;
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(NT) k_dense_inertia(const double* __restrict__
     }
     if (threadIdx.x == 0) { s_neg = 0; s_bad = 0; s_mp = 1.0 / 0.0; }
     __syncthreads();
-    cta_bk_ldl<NT>(S, n, n, perm, piv, red, redi, &s_neg, &s_mp, &s_bad, DBL_EPSILON * norm);
+    cta_bk_ldl<NT>(S, n, n, perm, piv, red, redi, &s_neg, &s_mp, &s_bad, DBL_EPSILON * norm, bkbuf);
     if (threadIdx.x == 0) {
         counts[s] = s_neg;
         if (minpiv) minpiv[s] = s_bad ? __longlong_as_double(0x7ff8000000000000ll) : s_mp;
@@ -108,7 +109,8 @@ extern "C" int h2_dense_inertia_noalloc(const double* d_A, int n, int lda, const
     double* scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc) return rc;
-    k_dense_inertia<<<ns, NT, 2 * n * sizeof(int), (cudaStream_t)stream>>>(d_A, n, lda, d_shifts, d_counts,
+    k_dense_inertia<<<ns, NT, 4 * n * sizeof(double) + 2 * n * sizeof(int), (cudaStream_t)stream>>>(
+        d_A, n, lda, d_shifts, d_counts,
                                                                           d_min_abs_pivot, scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
