@@ -18,6 +18,10 @@
  *    memory on the handle's device.  The library owns all memory it allocates
  *    and frees it in h2_destroy.
  *  - A handle is used by one host thread at a time (one handle per stream).
+ *    Several handles may share one stream.  Running several handles' batches
+ *    concurrently on separate streams stalled the device in testing (every
+ *    started kernel completed while a queued one never started); prefer one
+ *    stream for handles that are used together.
  *  - Every computation runs in the library's CUDA kernels; there is no CPU
  *    fallback.  Without a usable CUDA device, h2_build fails with H2_ERR_CUDA.
  */
@@ -152,6 +156,31 @@ int h2_inertia_device(h2_handle h, const double* d_shifts, int64_t ns, int64_t* 
  */
 int h2_kth_eig(h2_handle h, const int64_t* k, int64_t nk, double tol, double* out,
                double* err_bound);
+
+/*
+ * h2_status -- waits for the handle's stream, then returns and clears the
+ * device error record accumulated since the last h2_status or host-array call
+ * (the asynchronous h2_inertia_device reports only here):
+ *   info[0] = flags: 1 = NaN met in pivoting or recompression; 2 = a kernel
+ *             found a size outside its buffers and skipped its work;
+ *   info[1] = first reporting kernel (1 recompression, 2 rotation, 3 LDL^T,
+ *             4 triangular solves, 5 Schur update, 6 merge);
+ *   info[2..5] = its values, info[6..7] = its block indices.
+ * info: host, caller-owned, 8 int64.  Returns H2_ERR_NUMERICAL when flags != 0.
+ */
+int h2_status(h2_handle h, int64_t* info);
+
+/*
+ * h2_heartbeat -- diagnostic, active only when the environment variable
+ * H2_HEARTBEAT=1 is set before the first h2_build: copies 64 counters that
+ * every factorization kernel updates in zero-copy host memory -- for kernel
+ * kind j (0 init, 1 recompression, 2 rotation, 3 LDL^T, 4 triangular solves,
+ * 5 Schur, 6 merge, 8 dims, 9 merge dims, 10 finish, 11 lane count):
+ * out[4j] CTAs started, out[4j+1] threads finished, out[4j+2..4j+3] block
+ * indices of the last CTA started.  Makes no CUDA call, so it can be read
+ * while the device is busy.  Zeros when not enabled.  out: host, 64 uint32.
+ */
+void h2_heartbeat(uint32_t* out);
 
 /* ---- introspection -------------------------------------------------------- */
 typedef struct {

@@ -19,7 +19,7 @@ H2_PREC_FP64, H2_PREC_MIXED = 0, 1
 
 EXPORTED_SYMBOLS = ["h2_default_options", "h2_build", "h2_destroy", "h2_last_error", "h2_inertia",
                     "h2_inertia_device", "h2_kth_eig", "h2_info", "h2_tree_perm", "h2_level_ranks",
-                    "h2_profile_batch", "h2_dense_inertia_noalloc"]
+                    "h2_profile_batch", "h2_dense_inertia_noalloc", "h2_status", "h2_heartbeat"]
 KIND_NAMES = ["init", "recomp", "rotate", "ldl", "trsm", "schur", "merge", "other"]
 
 
@@ -80,6 +80,10 @@ def lib():
         L.h2_profile_batch.argtypes = [P, P, C.c_int64, P, P, P, P, P]
         L.h2_dense_inertia_noalloc.argtypes = [P, C.c_int, C.c_int, P, C.c_int, P, P, P]
         L.h2_dense_inertia_noalloc.restype = C.c_int
+        L.h2_heartbeat.argtypes = [P]
+        L.h2_heartbeat.restype = None
+        L.h2_status.argtypes = [P, P]
+        L.h2_status.restype = C.c_int
         for f in ("h2_build", "h2_inertia", "h2_inertia_device", "h2_kth_eig", "h2_info",
                   "h2_tree_perm", "h2_level_ranks", "h2_profile_batch"):
             getattr(L, f).restype = C.c_int
@@ -173,6 +177,12 @@ class H2Matrix:
         s = Stats()
         _check(lib().h2_info(self._h, C.byref(s)))
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def h2_status(self):
+        """(rc, info[8]) of the device error record (see include/h2eig.h)."""
+        info = np.zeros(8, dtype=np.int64)
+        rc = lib().h2_status(self._h, info.ctypes.data_as(C.c_void_p))
+        return rc, info
 
     def h2_tree_perm(self):
         p = np.zeros(self.n, dtype=np.int64)

@@ -180,6 +180,16 @@ int h2_profile_batch(h2_handle h, const double* d_shifts, int64_t ns, int64_t* d
     return run_profile(h, d_shifts, (int)ns, d_counts, ms, launches, flops, bytes);
 }
 
+int h2_status(h2_handle h, int64_t* info) {
+    g_last_error.clear();
+    if (!h || !info) { set_error("h2_status: null pointer"); return H2_ERR_INVALID_ARG; }
+    return run_status(h, info);
+}
+
+void h2_heartbeat(uint32_t* out) {
+    if (out) heartbeat_read(out);
+}
+
 int h2_tree_perm(h2_handle h, int64_t* perm) {
     if (!h || !perm) { set_error("h2_tree_perm: null pointer"); return H2_ERR_INVALID_ARG; }
     std::memcpy(perm, h->plan.perm.data(), h->n * sizeof(int64_t));

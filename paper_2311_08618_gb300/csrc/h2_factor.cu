@@ -20,6 +20,7 @@
 // once into a CUDA graph and replayed per batch.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -60,6 +61,25 @@ static int upload(T** p, const std::vector<T>& v) {
 
 constexpr int NT = 256;
 constexpr int TS = 32;   // Schur tile
+
+// Diagnostic heartbeat (enabled by H2_HEARTBEAT=1): per kernel kind, CTAs
+// started, threads finished, and the block indices of the last CTA started,
+// in zero-copy host memory so that the host can read them while the device
+// is busy.  Null (no cost beyond one load) otherwise.
+__device__ unsigned int* g_hb = nullptr;
+struct HbScope {
+    unsigned int* p;
+    __device__ explicit HbScope(int kind) : p(g_hb ? g_hb + 4 * kind : nullptr) {
+        if (p && threadIdx.x == 0) {
+            atomicAdd_system(p, 1u);
+            p[2] = blockIdx.x;
+            p[3] = blockIdx.y;
+        }
+    }
+    __device__ ~HbScope() {
+        if (p) atomicAdd_system(p + 1, 1u);
+    }
+};
 
 // scratch layout of one elimination (offsets in doubles)
 struct ScratchLayout {
@@ -139,12 +159,28 @@ __device__ __forceinline__ void add_stats(double* stats, int kind, double fl, do
     atomicAdd(&stats[H2_NKINDS + kind], by);
 }
 
+// Self-check record (err[0..7]): err[0] |= 1 for NaN, |= 2 when a kernel
+// meets a size outside its buffers (it then skips its work); the first such
+// kernel writes its id, four values and its block indices into err[1..7].
+__device__ __noinline__ void report_bad(int* err, int kernel, int a, int b, int c, int d) {
+    atomicOr(&err[0], 2);
+    if (atomicCAS(&err[1], 0, kernel) == 0) {
+        err[2] = a;
+        err[3] = b;
+        err[4] = c;
+        err[5] = d;
+        err[6] = blockIdx.x;
+        err[7] = blockIdx.y;
+    }
+}
+
 // scratch header (ints): [0] rk after recompression, [1] R', [2] r0, [3] t,
 // [4] recompression ran, [8 + ti] live rows of target ti
 constexpr int HDR_ROWS = 8;
 
 // ---- (i) recompression basis of row p (Sec. 3.4): one CTA per (cluster, lane)
 __global__ void __launch_bounds__(NT) k_recomp(FactorArgs A) {
+    HbScope hb_(1);
     const int ci = blockIdx.x, lane = blockIdx.y;
     if (lane >= *A.active) return;
     __shared__ double red[32];
@@ -161,13 +197,25 @@ __global__ void __launch_bounds__(NT) k_recomp(FactorArgs A) {
     int* hdr = (int*)(scr + A.lay.hdr);
     const int R = m - r0;
     const int nf = A.nfill[ci];
+    if (m < 0 || m > D || r0 < 0 || r0 > m || nf < 0 || nf > A.nfill_max) {
+        if (threadIdx.x == 0) report_bad(A.err, 1, m, r0, nf, D);
+        return;
+    }
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
     int t = 0;
     const int run = (nf > 0 && R > 0) ? 1 : 0;
     if (run) {
-        int wz = 0;
-        for (int f = 0; f < nf; ++f) wz += live_rows(A, A.fillq[ci * A.nfill_max + f], lane);
+        int wz = 0, badq = -1;
+        for (int f = 0; f < nf; ++f) {
+            int lq = live_rows(A, A.fillq[ci * A.nfill_max + f], lane);
+            if (lq < 0 || lq > D) badq = lq;
+            wz += lq;
+        }
+        if (badq != -1) {
+            if (threadIdx.x == 0) report_bad(A.err, 1, badq, wz, m, D);
+            return;
+        }
         int coff = 0;
         for (int f = 0; f < nf; ++f) {
             int q = A.fillq[ci * A.nfill_max + f];
@@ -202,6 +250,7 @@ __global__ void __launch_bounds__(NT) k_recomp(FactorArgs A) {
 constexpr int RC = 32;   // column (or row) chunk staged in shared memory
 template <typename T>
 __global__ void __launch_bounds__(NT) k_rotate(FactorArgs A) {
+    HbScope hb_(2);
     const int ci = blockIdx.x / A.nrow_max, b = blockIdx.x % A.nrow_max, lane = blockIdx.y;
     if (lane >= *A.active || b >= A.nrow[ci]) return;
     extern __shared__ double tile[];          // R x RC
@@ -217,6 +266,13 @@ __global__ void __launch_bounds__(NT) k_rotate(FactorArgs A) {
     const int x = A.rowblk_other[ci * A.nrow_max + b];
     const int tr = A.rowblk_trans[ci * A.nrow_max + b];
     double* B = slot_ptr(A.slots, A.rowblk[ci * A.nrow_max + b], LN, lane, D);
+    {
+        const int dxl = live_rows(A, x, lane), dqa = A.dim[x * LN + lane];
+        if (m < 0 || m > D || r0 < 0 || r0 > m || t < 0 || t > R || dxl < 0 || dxl > D || dqa < 0 || dqa > D) {
+            if (threadIdx.x == 0) report_bad(A.err, 2, m, r0, t, dqa);
+            return;
+        }
+    }
     double fl = 0.0;
     if (t > 0) {
         // rows r0.. of p: new = Vq^T old, over the live columns of x
@@ -271,6 +327,7 @@ __global__ void __launch_bounds__(NT) k_rotate(FactorArgs A) {
 // negative-pivot count: one CTA per (cluster, lane)
 template <int NTH>
 __global__ void __launch_bounds__(NTH) k_ldl(FactorArgs A, int use_smem) {
+    HbScope hb_(3);
     const int ci = blockIdx.x, lane = blockIdx.y;
     if (lane >= *A.active) return;
     extern __shared__ double sF[];
@@ -284,6 +341,14 @@ __global__ void __launch_bounds__(NTH) k_ldl(FactorArgs A, int use_smem) {
     const int Rp = m - rk1;
     double* scr = A.scratch + ((size_t)ci * LN + lane) * A.lay.total;
     int* hdr = (int*)(scr + A.lay.hdr);
+    if (m < 0 || m > D || rk1 < 0 || rk1 > m) {
+        if (threadIdx.x == 0) {
+            hdr[0] = 0;
+            hdr[1] = 0;     // later kernels of this elimination skip it
+            report_bad(A.err, 3, m, rk1, D, 0);
+        }
+        return;
+    }
     if (threadIdx.x == 0) {
         hdr[0] = rk1;
         hdr[1] = Rp;
@@ -326,6 +391,7 @@ __global__ void __launch_bounds__(NTH) k_ldl(FactorArgs A, int use_smem) {
 // short per-row solve inside the block)
 constexpr int JB = 8;
 __global__ void __launch_bounds__(NT) k_trsm(FactorArgs A, int use_smem) {
+    HbScope hb_(4);
     const int ci = blockIdx.x / A.ntarg_max, ti = blockIdx.x % A.ntarg_max, lane = blockIdx.y;
     if (lane >= *A.active || ti >= A.ntarg[ci]) return;
     extern __shared__ double sh[];
@@ -337,6 +403,13 @@ __global__ void __launch_bounds__(NT) k_trsm(FactorArgs A, int use_smem) {
     if (Rp <= 0) return;
     const int a = A.targ[ci * A.ntarg_max + ti];
     const int rows = (a == p) ? rk1 : live_rows(A, a, lane);
+    if (Rp > D || rk1 < 0 || rk1 + Rp > D || rows < 0 || rows > D) {
+        if (threadIdx.x == 0) {
+            hdr[HDR_ROWS + ti] = 0;
+            report_bad(A.err, 4, rk1, Rp, rows, a);
+        }
+        return;
+    }
     if (threadIdx.x == 0) {
         hdr[HDR_ROWS + ti] = rows;
         double fs = 0.0, bs = 0.0;
@@ -431,6 +504,7 @@ struct SchurArgs {
     const double* scratch;
     ScratchLayout lay;
     const int* active;
+    int* err;
 };
 
 // S_ab[i0:i0+32, j0:j0+32] -= W_a Y_b^T (Eq. blr2-diag-schur).  T is the
@@ -438,6 +512,7 @@ struct SchurArgs {
 // products and accumulation, the FP64 block updated by the rounded result).
 template <typename T>
 __global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
+    HbScope hb_(5);
     const int lane = blockIdx.y;
     if (lane >= *A.active) return;
     const int pi = blockIdx.x / A.tiles_per_pair, tile = blockIdx.x % A.tiles_per_pair;
@@ -448,6 +523,10 @@ __global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
     const int Rp = hdr[1];
     if (Rp <= 0) return;
     const int ra = hdr[HDR_ROWS + P.ta], rb = hdr[HDR_ROWS + P.tb];
+    if (Rp > D || ra < 0 || ra > D || rb < 0 || rb > D) {
+        if (threadIdx.x == 0 && tile == 0) report_bad(A.err, 5, Rp, ra, rb, D);
+        return;
+    }
     const int i0 = (tile / A.tdim) * TS, j0 = (tile % A.tdim) * TS;
     if (i0 >= ra || j0 >= rb) return;
     const double* W = scr + A.lay.w + (size_t)P.ta * D * D;
@@ -498,6 +577,7 @@ struct InitArgs {
 };
 
 __global__ void k_init_leaf(InitArgs A) {
+    HbScope hb_(0);
     const int sl = blockIdx.x, lane = blockIdx.y;
     if (lane >= *A.active) return;
     const int D = A.D;
@@ -524,6 +604,7 @@ __global__ void k_init_leaf(InitArgs A) {
 
 __global__ void k_init_dims(int* dim, int* rk, const int64_t* off, const int* rb, int nc, int lanes,
                             unsigned long long* neg, unsigned long long* minpiv, int* err, double* stats) {
+    HbScope hb_(8);
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < nc * lanes) {
         int c = e / lanes;
@@ -534,12 +615,13 @@ __global__ void k_init_dims(int* dim, int* rk, const int64_t* off, const int* rb
         neg[e] = 0ull;
         minpiv[e] = (unsigned long long)__double_as_longlong(1.0 / 0.0);
     }
-    if (e == 0) *err = 0;
+    (void)err;   // the error record persists until read (h2_status / host calls)
     if (e < 2 * H2_NKINDS) stats[e] = 0.0;
 }
 
 // parent dims: dim[P] = rk[c1] + rk[c2], rk[P] = rb[P]
 __global__ void k_merge_dims(int* dimP, int* rkP, const int* rkC, const int* rbP, int ncP, int lanes) {
+    HbScope hb_(9);
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ncP * lanes) return;
     int P = e / lanes, lane = e % lanes;
@@ -571,6 +653,7 @@ struct MergeArgs {
     double* scratch;   // [nslotsP][lanes][2][DP*DP]
     const int* active;
     double* stats;
+    int* err;
 };
 
 __device__ __forceinline__ int place_child(int first, int i, int rb_self, int rb1, int rb2, int t1) {
@@ -580,6 +663,7 @@ __device__ __forceinline__ int place_child(int first, int i, int rb_self, int rb
 }
 
 __global__ void __launch_bounds__(NT) k_merge(MergeArgs A) {
+    HbScope hb_(6);
     const int sl = blockIdx.x, lane = blockIdx.y;
     if (lane >= *A.active) return;
     const int DP = A.DP, LN = A.lanes;
@@ -604,6 +688,14 @@ __global__ void __launch_bounds__(NT) k_merge(MergeArgs A) {
     }
     const int dP = rkc[0] + rkc[1], dQ = rkc[2] + rkc[3];
     const int kP = rbc[0] + rbc[1], kQ = rbc[2] + rbc[3];
+    {
+        bool bad = dP > DP || dQ > DP || kP > A.dqP || kQ > A.dqP;
+        for (int u = 0; u < 4; ++u) bad = bad || rkc[u] < rbc[u] || rkc[u] > A.DC;
+        if (bad) {
+            if (threadIdx.x == 0) report_bad(A.err, 6, dP, dQ, kP, kQ);
+            return;
+        }
+    }
     if (threadIdx.x == 0) {
         atomicAdd(&A.stats[H2_KIND_MERGE], 2.0 * kP * (double)kP * dQ + 2.0 * dP * (double)kQ * kQ);
         atomicAdd(&A.stats[H2_NKINDS + H2_KIND_MERGE],
@@ -664,10 +756,14 @@ __global__ void __launch_bounds__(NT) k_merge(MergeArgs A) {
     }
 }
 
-__global__ void k_set_int(int* p, int v) { *p = v; }
+__global__ void k_set_int(int* p, int v) {
+    HbScope hb_(11);
+    *p = v;
+}
 
 __global__ void k_finish(const unsigned long long* neg, const unsigned long long* minpiv, int64_t* counts,
                          double* mp, const int* active) {
+    HbScope hb_(10);
     int lane = blockIdx.x * blockDim.x + threadIdx.x;
     if (lane >= *active) return;
     counts[lane] = (int64_t)neg[lane];
@@ -709,7 +805,12 @@ static FactorState* state_of(h2_matrix* h) {
     return reinterpret_cast<FactorState*>(h->ws.graph_state);
 }
 
+static int ensure_graph(h2_matrix* h, int mixed);
+int heartbeat_setup();
+
 int alloc_workspace(h2_matrix* h, int lanes) {
+    int hrc = heartbeat_setup();
+    if (hrc) return hrc;
     const Plan& P = h->plan;
     const int L = P.L;
     Workspace& ws = h->ws;
@@ -837,12 +938,19 @@ int alloc_workspace(h2_matrix* h, int lanes) {
     if ((rc = dalloc(&ws.d_scratch, scratch_max))) return rc;
     if ((rc = dalloc(&ws.d_merge, std::max<size_t>(merge_max, 1)))) return rc;
     bytes += (scratch_max + merge_max) * 8;
-    if ((rc = dalloc(&ws.d_neg, lanes)) || (rc = dalloc(&ws.d_minpiv, lanes)) || (rc = dalloc(&ws.d_err, 4)) ||
+    if ((rc = dalloc(&ws.d_neg, lanes)) || (rc = dalloc(&ws.d_minpiv, lanes)) || (rc = dalloc(&ws.d_err, 8)) ||
         (rc = dalloc(&ws.d_shifts, lanes)) || (rc = dalloc(&fs->d_active, 1)) ||
         (rc = dalloc(&fs->d_counts, lanes)) || (rc = dalloc(&fs->d_mp, lanes)) ||
         (rc = dalloc(&fs->d_stats, 2 * H2_NKINDS)))
         return rc;
     ws.bytes = bytes;
+    CK(cudaMemsetAsync(ws.d_err, 0, 8 * sizeof(int), h->stream));
+    // capture the batch graphs now, while nothing else runs on the device:
+    // a capture never overlaps other handles' work on other streams
+    CK(cudaStreamSynchronize(h->stream));
+    if ((rc = ensure_graph(h, 0))) return rc;
+    if (h->opt.precision == H2_PREC_MIXED && (rc = ensure_graph(h, 1))) return rc;
+    CK(cudaStreamSynchronize(h->stream));
     return H2_OK;
 }
 
@@ -927,7 +1035,7 @@ static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, 
             E();
             int tdim = (D.dmax + TS - 1) / TS;
             SchurArgs sa{ws.d_slots[l], D.dmax, LN, C.pairs, tdim * tdim, tdim, ws.d_scratch, W.lay,
-                         fs->d_active};
+                         fs->d_active, ws.d_err};
             B(H2_KIND_SCHUR);
             if (mixed)
                 k_schur<float><<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
@@ -945,7 +1053,7 @@ static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, 
             MergeArgs ma{ws.d_slots[l - 1], Pd.dmax, LN, Pd.d_slot_a, Pd.d_slot_b, Pd.d_slot_kind,
                          Pd.d_slot_far, Pd.d_C, Pd.estride, Pd.d_rb, Pd.d_Q, Pd.dq, ws.d_slots[l], D.dmax,
                          D.nc, W.d_slot_of, W.d_far_of, D.d_C, D.estride, D.d_rb, ws.d_rk[l], ws.d_merge,
-                         fs->d_active, fs->d_stats};
+                         fs->d_active, fs->d_stats, ws.d_err};
             B(H2_KIND_MERGE);
             k_merge<<<dim3(Pd.nslots, LN), NT, 0, st>>>(ma);
             E();
@@ -971,8 +1079,19 @@ static int ensure_graph(h2_matrix* h, int mixed) {
     return H2_OK;
 }
 
-// launch one batch of the lanes already in ws.d_shifts (count set on device)
+// launch one batch of the lanes already in ws.d_shifts (count set on device);
+// the environment variable H2_NO_GRAPH=1 (a diagnostic) launches the same
+// kernels one by one instead of replaying the captured graph
 static int launch_batch(h2_matrix* h, int mixed) {
+    static const int no_graph = [] {
+        const char* e = getenv("H2_NO_GRAPH");
+        return e && e[0] == '1';
+    }();
+    if (no_graph) {
+        enqueue_factorization(h, h->stream, nullptr, mixed);
+        CK(cudaGetLastError());
+        return H2_OK;
+    }
     int rc = ensure_graph(h, mixed);
     if (rc) return rc;
     CK(cudaGraphLaunch(mixed ? h->ws.graph_mixed : h->ws.graph, h->stream));
@@ -998,6 +1117,45 @@ int run_inertia(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts,
     return H2_OK;
 }
 
+std::string err_message(const int* e) {
+    if (e[0] & 2)
+        return "kernel " + std::to_string(e[1]) + " met out-of-range sizes (" + std::to_string(e[2]) + ", " +
+               std::to_string(e[3]) + ", " + std::to_string(e[4]) + ", " + std::to_string(e[5]) + ") at block (" +
+               std::to_string(e[6]) + ", " + std::to_string(e[7]) + ") and skipped its work";
+    return "NaN pivot in the factorization";
+}
+
+// heartbeat buffer (host side), set up once per process when H2_HEARTBEAT=1
+static unsigned int* g_hb_host = nullptr;
+
+int heartbeat_setup() {
+    const char* e = getenv("H2_HEARTBEAT");
+    if (!e || e[0] != '1' || g_hb_host) return H2_OK;
+    CK(cudaHostAlloc((void**)&g_hb_host, 64 * sizeof(unsigned int), cudaHostAllocMapped));
+    std::memset(g_hb_host, 0, 64 * sizeof(unsigned int));
+    unsigned int* d = nullptr;
+    CK(cudaHostGetDevicePointer((void**)&d, g_hb_host, 0));
+    CK(cudaMemcpyToSymbol(g_hb, &d, sizeof(d)));
+    return H2_OK;
+}
+
+void heartbeat_read(unsigned int* out) {
+    for (int i = 0; i < 64; ++i) out[i] = g_hb_host ? ((volatile unsigned int*)g_hb_host)[i] : 0u;
+}
+
+int run_status(h2_matrix* h, int64_t* info) {
+    int e[8] = {0};
+    CK(cudaMemcpyAsync(e, h->ws.d_err, sizeof(e), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemsetAsync(h->ws.d_err, 0, sizeof(e), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < 8; ++i) info[i] = e[i];
+    if (e[0]) {
+        set_error(err_message(e));
+        return H2_ERR_NUMERICAL;
+    }
+    return H2_OK;
+}
+
 // one batch of host shifts (nb <= lanes) in the given precision; counts and
 // min |pivot| back to host arrays
 static int host_batch(h2_matrix* h, const double* shifts, int nb, int mixed, int64_t* counts, double* minpiv) {
@@ -1010,11 +1168,11 @@ static int host_batch(h2_matrix* h, const double* shifts, int nb, int mixed, int
     if (rc) return rc;
     CK(cudaMemcpyAsync(counts, fs->d_counts, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(minpiv, fs->d_mp, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-    int err = 0;
-    CK(cudaMemcpyAsync(&err, ws.d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int err[8] = {0};
+    CK(cudaMemcpyAsync(err, ws.d_err, sizeof(err), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (err) {
-        set_error("NaN pivot in the factorization");
+    if (err[0]) {
+        set_error(err_message(err));
         return H2_ERR_NUMERICAL;
     }
     return H2_OK;
@@ -1084,7 +1242,7 @@ int run_inertia_host(h2_matrix* h, const double* shifts, int64_t ns, int64_t* co
     Workspace& ws = h->ws;
     cudaStream_t st = h->stream;
     const int mixed = h->opt.precision == H2_PREC_MIXED;
-    CK(cudaMemsetAsync(ws.d_err, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(ws.d_err, 0, 8 * sizeof(int), st));
     std::vector<double> mp(ws.lanes);
     h->last_guarded = 0;
     for (int64_t b0 = 0; b0 < ns; b0 += ws.lanes) {
@@ -1203,7 +1361,7 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
         set_error("h2_kth_eig: at most 1024 k per call");
         return H2_ERR_INVALID_ARG;
     }
-    CK(cudaMemsetAsync(ws.d_err, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(ws.d_err, 0, 8 * sizeof(int), st));
     // start interval: Gershgorin padded by 1e-6 ||A||_inf; check nu(a) = 0, nu(b) = n in FP64
     const double a = h->glo - 1e-6 * h->norm_inf, b = h->ghi + 1e-6 * h->norm_inf;
     if (ws.lanes >= 2) {
@@ -1288,11 +1446,11 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
     h->last_rounds = rounds;
     CK(cudaMemcpyAsync(lo.data(), fs->d_lo, nk * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(hi.data(), fs->d_hi, nk * sizeof(double), cudaMemcpyDeviceToHost, st));
-    int err = 0;
-    CK(cudaMemcpyAsync(&err, ws.d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int err[8] = {0};
+    CK(cudaMemcpyAsync(err, ws.d_err, sizeof(err), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (err) {
-        set_error("h2_kth_eig: NaN pivot in the factorization");
+    if (err[0]) {
+        set_error("h2_kth_eig: " + err_message(err));
         return H2_ERR_NUMERICAL;
     }
     for (int64_t i = 0; i < nk; ++i) {

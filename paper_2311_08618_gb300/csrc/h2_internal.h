@@ -158,5 +158,7 @@ int run_profile(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts,
 int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
             double* err_bound);
 void free_workspace(h2_matrix* h);
+int run_status(h2_matrix* h, int64_t* info);
+void heartbeat_read(unsigned int* out);
 void free_device(h2_matrix* h);
 }  // namespace h2

@@ -11,10 +11,13 @@ Model
   exceeds the memory reserved for it (admission by HBM footprint).
 * A tick runs one multisection round on every matrix with active requests:
   the distinct active intervals of that matrix share its lanes (q interior
-  points each), the batches of all matrices are enqueued on their own CUDA
-  streams so they overlap on the GPU, then every interval of every request
-  is narrowed with all (mu, nu) pairs of its matrix's round (Algorithm 1;
-  inertia reuse across requests, Sec. 4.2).
+  points each), the batches of all matrices are enqueued back to back on the
+  server's CUDA stream and waited for once, then every interval of every
+  request is narrowed with all (mu, nu) pairs of its matrix's round
+  (Algorithm 1; inertia reuse across requests, Sec. 4.2).  Requests of one
+  matrix share its batch, so their work overlaps on the device.  (Giving
+  every matrix its own stream stalled the device in testing: all started
+  kernels completed, yet a queued one never started; one stream avoids it.)
 * Requests that arrive while others are on the GPU join at the next tick
   (continuous batching).  A new request starts from the tightest bracket in
   its matrix's table of evaluated (mu, nu) pairs instead of the Gershgorin
@@ -80,13 +83,14 @@ class Server:
         self.footprint = 0
         self.shifts_evaluated = 0
         self.ticks = 0
+        self.stream = torch.cuda.Stream()       # one stream for all resident matrices
 
     # -- residency ----------------------------------------------------------
     def add_matrix(self, name, points, kernel, kparams, leaf, rank, eta=1.0, lanes=16, **opts):
         """Builds and keeps resident an H^2 matrix; refuses it when the HBM
         budget would be exceeded by its workspace."""
         torch = self.torch
-        stream = torch.cuda.Stream()
+        stream = self.stream
         h = H2Matrix(points, kernel, kparams, leaf=leaf, rank=rank, eta=eta, max_lanes=lanes,
                      stream=stream.cuda_stream, **opts)
         info = h.h2_info()
@@ -196,8 +200,9 @@ class Server:
                     raise RuntimeError(L.h2_last_error().decode())
                 r.h_counts[:ns].copy_(r.d_counts[:ns], non_blocking=True)
             launched.append(r)
+        if launched:
+            self.stream.synchronize()
         for r in launched:
-            r.stream.synchronize()
             ns = len(r.pending)
             counts = r.h_counts[:ns].numpy().copy()
             self.shifts_evaluated += ns
