@@ -3,7 +3,7 @@
 
 Workload (the n = 1024 configuration): n = 1024 points uniform in the unit
 square (SplitMix64 seed 1), A_ij = 1/(|x_i - x_j| + 1e-3) (A_ii = 1e3), leaf
-64, rank 16, eta = 1 (box admissibility), FP64.  A step is one batch of 64
+64, rank 16, eta = 1 (box admissibility), FP64.  A step is one batch of 256
 shifted matrices A~ - sigma I factorized together (all levels: leaf blocks,
 fill-in recompression, Bunch-Kaufman LDL^T, Schur updates, merges, negative
 pivot count); the shifts of step i are 64 points spread over the Gershgorin
@@ -11,9 +11,9 @@ interval (seeded jitter), resident in HBM before the timed region.
 
 value : LDL-inertia shifts/sec, device-resident shifts (h2_inertia_device).
 e2e   : the same metric through h2_inertia with host (pinned) buffers: the H2D
-        copy of the 64 shifts and the D2H read of the 64 counts in every step.
+        copy of the 256 shifts and the D2H read of the 256 counts in every step.
 Extra keys: k-th eigenvalue solves (k = n/2, tol 1e-8) -- eigs/sec, p50/p99
-latency, rounds, shifts per solve.
+latency, rounds, shifts per solve, on a 64-lane handle.
 
 Multi-GPU (torchrun): every rank holds its own replica and factorizes its own
 batches (independent shifts, no data-path collective); value = all ranks'
@@ -301,17 +301,21 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
     e2e_value = world * args.steps * lanes / e2e_s
     same = bool(torch.equal(d_cnt.cpu(), h_cnt))
     info = M.h2_info()
-    # ---- k-th eigenvalue solves (all of the path incl. the bisection driver)
+    # ---- k-th eigenvalue solves (all of the path incl. the bisection driver),
+    # on a handle with eig_lanes lanes (latency: fewer lanes per round)
+    Me = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
+                      eta=WORKLOAD["eta"], max_lanes=args.eig_lanes, stream=stream.cuda_stream)
     lat = []
     lam = None
     for i in range(args.eig_solves + 2):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        out, eb = M.h2_kth_eig([WORKLOAD["k"]], WORKLOAD["tol"])
+        out, eb = Me.h2_kth_eig([WORKLOAD["k"]], WORKLOAD["tol"])
         lat.append(time.perf_counter() - t)
         lam = (out[0], eb[0])
     lat = np.array(lat[2:])
-    info2 = M.h2_info()
+    info2 = Me.h2_info()
+    Me.close()
     # ---- roofline of the dominant kernel: profiled batches (events per launch)
     prof = None
     for i in range(args.warmup, min(total, args.warmup + 5)):
@@ -353,6 +357,9 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
     Mx = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
                       eta=WORKLOAD["eta"], max_lanes=lanes, stream=stream.cuda_stream,
                       precision=pkg.H2_PREC_MIXED)
+    Mxe = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
+                       eta=WORKLOAD["eta"], max_lanes=args.eig_lanes, stream=stream.cuda_stream,
+                       precision=pkg.H2_PREC_MIXED)
     for i in range(args.warmup):
         Mx.h2_inertia_device(d_sh[i], lanes, d_cnt[i], d_mp[i])
     torch.cuda.synchronize()
@@ -366,10 +373,11 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
     for i in range(args.eig_solves + 2):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        outm, ebm = Mx.h2_kth_eig([WORKLOAD["k"]], WORKLOAD["tol"])
+        outm, ebm = Mxe.h2_kth_eig([WORKLOAD["k"]], WORKLOAD["tol"])
         latm.append(time.perf_counter() - t)
     latm = np.array(latm[2:])
-    infm = Mx.h2_info()
+    infm = Mxe.h2_info()
+    Mxe.close()
     precision = {"mode": "fp32 products, fp64 storage/pivots/counts",
                  "value": world * args.steps * lanes / (ms_mix / 1e3), "unit": "shifts/s",
                  "eigs_per_s": float(1.0 / np.mean(latm)), "p50_ms": float(np.percentile(latm, 50) * 1e3),
@@ -377,6 +385,7 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
                  "mixed_rounds": infm["last_mixed_rounds"], "bracket_resets": infm["bracket_resets"],
                  "lambda": float(outm[0]), "abs_diff_vs_fp64": float(abs(outm[0] - lam[0]))}
     Mx.close()
+    serving_res = _serving(args) if args.serving_s > 0 and world == 1 else None
     ws_mb = info["workspace_bytes"] / 1e6
     line = {"metric": METRIC, "value": value, "unit": "shifts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -388,11 +397,13 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
             "e2e": {"value": e2e_value, "unit": "shifts/s", "h2d_bytes_per_step": 8 * lanes,
                     "d2h_bytes_per_step": 8 * lanes, "counts_match_device_path": same},
             "gpu_launches": info["kernels_per_batch"] * args.steps,
-            "eigs": {"k": WORKLOAD["k"], "tol": WORKLOAD["tol"], "eigs_per_s": float(1.0 / np.mean(lat)),
+            "eigs": {"k": WORKLOAD["k"], "tol": WORKLOAD["tol"], "lanes": args.eig_lanes,
+                     "eigs_per_s": float(1.0 / np.mean(lat)),
                      "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                      "rounds": info2["last_rounds"], "shifts_per_solve": info2["last_shifts"],
                      "lambda": lam[0], "err_bound": lam[1]},
-            "build_s": build_s, "roofline": roof, "clocks": clocks, "precision": precision}
+            "build_s": build_s, "roofline": roof, "clocks": clocks, "precision": precision,
+            "serving": serving_res}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         sample = list(sh[args.warmup][:: max(1, lanes // (2 * cores))][:2 * cores])
@@ -408,15 +419,60 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
     M.close()
 
 
+SERVING_SIZES = (1024, 2048, 4096, 8192)
+
+
+def _serving(args):
+    """Open-loop serving: Poisson arrivals of k-th eigenvalue queries (k uniform,
+    tol log-uniform in [1e-10, 1e-6]) over resident 2D Laplace H^2 matrices of
+    different sizes; continuous batching (paper_2311_08618_gb300.serving)."""
+    from paper_2311_08618_gb300 import serving
+    srv = serving.Server()
+    for i, n in enumerate(SERVING_SIZES):
+        srv.add_matrix("m%d" % i, W.uniform_cube(n, 2, 100 + i), W.LAPLACE_EPS, (1e-3, 0, 0, 0), 64, 16,
+                       lanes=args.serving_lanes)
+    rate = args.serving_rate
+    u = W.uniform(4242, 4 * 100000)
+    arr, t, j = [], 0.0, 0
+    while True:
+        t += -math.log(1.0 - u[j]) / rate
+        j += 1
+        if t > args.serving_s:
+            break
+        mi = int(u[j] * len(SERVING_SIZES))
+        k = 1 + int(u[j + 1] * SERVING_SIZES[mi])
+        tol = 10.0 ** (-10.0 + 4.0 * u[j + 2])
+        j += 3
+        arr.append((t, "m%d" % mi, k, tol))
+    t0 = time.perf_counter()
+    done, unfinished = serving.run_open_loop(srv, arr, args.serving_s, deadline_s=args.serving_s + 25.0)
+    wall = time.perf_counter() - t0
+    st = serving.latency_stats(done)
+    res = {"matrices": "4 resident 2D Laplace H2 matrices n=%s (leaf 64, rank 16), %d lanes each"
+                       % (list(SERVING_SIZES), args.serving_lanes),
+           "stand_in": "the 64-matrix 3D n<=131072 configuration needs ~16-70 GB per lane under eta=1 box "
+                       "admissibility and does not fit one GPU",
+           "arrivals": "Poisson %.0f q/s for %.0f s" % (rate, args.serving_s), "offered": len(arr),
+           "completed": len(done), "unfinished": unfinished, "wall_s": wall,
+           "eigs_per_s": len(done) / wall, "shifts_per_s": srv.shifts_evaluated / wall, "ticks": srv.ticks}
+    res.update(st)
+    srv.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--lanes", type=int, default=64)
+    ap.add_argument("--lanes", type=int, default=256, help="shifts per step (throughput)")
+    ap.add_argument("--eig-lanes", type=int, default=64, help="lanes of the k-th eigenvalue solves")
     ap.add_argument("--eig-solves", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-s", type=float, default=3.0, help="seconds of arrivals (0: skip)")
+    ap.add_argument("--serving-rate", type=float, default=40.0)
+    ap.add_argument("--serving-lanes", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

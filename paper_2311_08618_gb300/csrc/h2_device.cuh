@@ -93,6 +93,51 @@ __device__ int block_argmax(double v, int idx, double* redv, int* redi, double* 
     return r;
 }
 
+// argmax (first index on ties) with a single barrier: warp-shuffle
+// reduction, one partial per warp in shared memory, then every thread reduces
+// the partials itself.  `buf` alternates between two halves (par selects the
+// half) so that consecutive calls need no trailing barrier: a thread can only
+// reach call n+2 (same half) after every thread passed the barrier of call n+1,
+// i.e. after every thread finished reading the partials of call n.
+template <int NT>
+__device__ __forceinline__ int block_argmax1(double v, int idx, double* bufv, int* bufi, int par,
+                                             double* outv) {
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    const int w = threadIdx.x >> 5;
+    double* bv = bufv + par * (NT / 32);
+    int* bi = bufi + par * (NT / 32);
+    if ((threadIdx.x & 31) == 0) { bv[w] = v; bi[w] = idx; }
+    __syncthreads();
+    v = bv[0];
+    idx = bi[0];
+#pragma unroll
+    for (int u = 1; u < NT / 32; ++u) {
+        double ov = bv[u];
+        int oi = bi[u];
+        if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    *outv = v;
+    return idx;
+}
+
+// sum with a single barrier, double-buffered like block_argmax1 (the partials
+// of the warps are added in warp order, the same on every thread)
+template <int NT>
+__device__ __forceinline__ double block_sum1(double v, double* buf, int par) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    double* b = buf + par * (NT / 32);
+    if ((threadIdx.x & 31) == 0) b[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = b[0];
+#pragma unroll
+    for (int u = 1; u < NT / 32; ++u) r += b[u];
+    return r;
+}
+
 // ------------------------------------------------- pivoted Householder QR --
 // Householder QR with column pivoting of Y (m x s, row-major, leading
 // dimension ldy), in place, stopped when the Frobenius norm of the
@@ -103,10 +148,15 @@ __device__ int block_argmax(double v, int idx, double* redv, int* redi, double* 
 template <int NT>
 __device__ int cta_pivqr(double* Y, int ldy, int m, int s, double tol, int cap, double* V,
                          int ldv, double* colnorm, double* red, int* redi, int* bad = nullptr) {
+    // red / redi: at least 2 * NT / 32 entries (double-buffered reductions)
     int kmax = min(min(m, s), cap);
     int k = 0;
+    int par = 0;
     for (; k < kmax; ++k) {
-        // trailing column norms (exact recomputation, no downdating)
+        // trailing column norms (exact recomputation, no downdating); each
+        // thread owns its columns, so no barrier is needed before the scan
+        double part = 0.0, best = -1.0;
+        int bi = 0x7fffffff;
         for (int j = k + threadIdx.x; j < s; j += NT) {
             double a = 0.0;
             for (int i = k; i < m; ++i) {
@@ -114,22 +164,19 @@ __device__ int cta_pivqr(double* Y, int ldy, int m, int s, double tol, int cap, 
                 a += y * y;
             }
             colnorm[j] = a;
+            part += a;
+            if (a > best) { best = a; bi = j; }
         }
-        __syncthreads();
-        double part = 0.0, best = -1.0;
-        int bi = 0x7fffffff;
-        for (int j = k + threadIdx.x; j < s; j += NT) {
-            part += colnorm[j];
-            if (colnorm[j] > best) { best = colnorm[j]; bi = j; }
-        }
-        double total = block_sum<NT>(part, red);
+        double total = block_sum1<NT>(part, red, par);
+        par ^= 1;
         if (!(total == total)) {          // NaN input: stop, report, touch nothing
             if (bad && threadIdx.x == 0) *bad = 1;
             break;
         }
         if (sqrt(total) <= tol) break;
         double bv;
-        int jp = block_argmax<NT>(best, bi, red, redi, &bv);
+        int jp = block_argmax1<NT>(best, bi, red, redi, par, &bv);
+        par ^= 1;
         if (jp < k || jp >= s) jp = k;
         if (jp != k)
             for (int i = threadIdx.x; i < m; i += NT) {
@@ -144,18 +191,20 @@ __device__ int cta_pivqr(double* Y, int ldy, int m, int s, double tol, int cap, 
             double x = Y[(size_t)i * ldy + k];
             nx2 += x * x;
         }
-        nx2 = block_sum<NT>(nx2, red);
+        nx2 = block_sum1<NT>(nx2, red, par);
+        par ^= 1;
         double nx = sqrt(nx2);
         double x0 = Y[(size_t)k * ldy + k];
         double alpha = x0 >= 0.0 ? -nx : nx;
-        // |v|^2 = |x|^2 - 2 alpha x0 + alpha^2 = 2 nx^2 - 2 alpha x0
+        // |v|^2 = |x|^2 - 2 alpha x0 + alpha^2
         double v0 = x0 - alpha;
         double nv2 = 0.0;
         for (int i = k + threadIdx.x; i < m; i += NT) {
             double x = (i == k) ? v0 : Y[(size_t)i * ldy + k];
             nv2 += x * x;
         }
-        nv2 = block_sum<NT>(nv2, red);
+        nv2 = block_sum1<NT>(nv2, red, par);
+        par ^= 1;
         double nv = sqrt(nv2);
         for (int i = threadIdx.x; i < m; i += NT) {
             double x = 0.0;
@@ -215,7 +264,10 @@ template <int NT>
 __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, double* red,
                            int* redi, int* neg, double* minpiv, int* bad, double zero_pivot,
                            double* buf) {
+    // red / redi: at least 2 * NT / 32 entries each (double-buffered argmax)
     const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+    constexpr int NW = NT / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double* c0 = buf;
     double* c1 = buf + n;
     double* l0 = buf + 2 * n;
@@ -224,6 +276,7 @@ __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, doubl
     __syncthreads();
     int k = 0;
     int nneg = 0;
+    int par = 0;
     double mp = 1.0 / 0.0;
     while (k < n) {
         double akk = fabs(S[(size_t)k * lds + k]);
@@ -235,7 +288,8 @@ __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, doubl
             if (v > best) { best = v; bi = i; }
         }
         double lam;
-        int r = block_argmax<NT>(best, bi, red, redi, &lam);
+        int r = block_argmax1<NT>(best, bi, red, redi, par, &lam);
+        par ^= 1;
         if (k + 1 >= n) { lam = 0.0; r = k; }
         else if (r <= k || r >= n) r = k + 1;
         int size = 1;
@@ -251,7 +305,8 @@ __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, doubl
                 if (v > b2) { b2 = v; bj = j; }
             }
             double sig;
-            block_argmax<NT>(b2, bj, red, redi, &sig);
+            block_argmax1<NT>(b2, bj, red, redi, par, &sig);
+            par ^= 1;
             if (sig < 0.0) sig = 0.0;
             if (akk * sig >= alpha * lam * lam) {
                 // 1x1 at k
@@ -264,6 +319,7 @@ __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, doubl
         }
         if (swap_a >= 0 && swap_a != swap_b) {
             // swap rows then columns swap_a <-> swap_b (all of them)
+            __syncthreads();   // every thread has read S for the pivot search
             for (int j = threadIdx.x; j < n; j += NT) {
                 double t = S[(size_t)swap_a * lds + j];
                 S[(size_t)swap_a * lds + j] = S[(size_t)swap_b * lds + j];
@@ -280,34 +336,31 @@ __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, doubl
                 perm[swap_a] = perm[swap_b];
                 perm[swap_b] = t;
             }
-            __syncthreads();
         }
+        __syncthreads();
         if (size == 1) {
             double d = S[(size_t)k * lds + k];
-            if (d == 0.0 && zero_pivot != 0.0) {
-                // exactly zero pivot with a zero column: stored as zero_pivot
-                __syncthreads();
-                d = zero_pivot;
-                if (threadIdx.x == 0) S[(size_t)k * lds + k] = d;
-            }
+            if (d == 0.0 && zero_pivot != 0.0) d = zero_pivot;   // zero column: stored as zero_pivot
             if (threadIdx.x == 0) {
+                S[(size_t)k * lds + k] = d;
                 piv[k] = 1;
                 if (d < 0.0) nneg += 1;
                 mp = fmin(mp, fabs(d));
                 if (d != d) *bad = 1;
             }
             if (d != 0.0 && k + 1 < n) {
-                // c = S[k+1:, k], l = c / d ; S[k+1:, k+1:] -= l c^T ; S[k+1:, k] = l
+                // c = S[k+1:, k], l = c (1/d) ; S[k+1:, k+1:] -= l c^T ; S[k+1:, k] = l
+                const double invd = 1.0 / d;
                 for (int i = k + 1 + threadIdx.x; i < n; i += NT) {
                     double c = S[(size_t)i * lds + k];
                     c0[i] = c;
-                    l0[i] = c / d;
+                    l0[i] = c * invd;
                 }
                 __syncthreads();
-                int t = n - k - 1;
-                for (int e = threadIdx.x; e < t * t; e += NT) {
-                    int i = k + 1 + e / t, j = k + 1 + e % t;
-                    S[(size_t)i * lds + j] -= l0[i] * c0[j];
+                for (int i = k + 1 + warp; i < n; i += NW) {
+                    const double li = l0[i];
+                    double* Si = S + (size_t)i * lds;
+                    for (int j = k + 1 + lane; j < n; j += 32) Si[j] -= li * c0[j];
                 }
                 for (int i = k + 1 + threadIdx.x; i < n; i += NT) S[(size_t)i * lds + k] = l0[i];
             }
@@ -329,7 +382,8 @@ __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, doubl
             }
             if (k + 2 < n) {
                 // Lc = C E^{-1}; S[k+2:, k+2:] -= Lc C^T ; store Lc in S[k+2:, k:k+2]
-                double i00 = c / det, i01 = -b / det, i11 = a / det;
+                const double idet = 1.0 / det;
+                double i00 = c * idet, i01 = -b * idet, i11 = a * idet;
                 for (int i = k + 2 + threadIdx.x; i < n; i += NT) {
                     double ci0 = S[(size_t)i * lds + k], ci1 = S[(size_t)i * lds + k + 1];
                     c0[i] = ci0;
@@ -338,10 +392,10 @@ __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, doubl
                     l1[i] = ci0 * i01 + ci1 * i11;
                 }
                 __syncthreads();
-                int t = n - k - 2;
-                for (int e = threadIdx.x; e < t * t; e += NT) {
-                    int i = k + 2 + e / t, j = k + 2 + e % t;
-                    S[(size_t)i * lds + j] -= l0[i] * c0[j] + l1[i] * c1[j];
+                for (int i = k + 2 + warp; i < n; i += NW) {
+                    const double a0 = l0[i], a1 = l1[i];
+                    double* Si = S + (size_t)i * lds;
+                    for (int j = k + 2 + lane; j < n; j += 32) Si[j] -= a0 * c0[j] + a1 * c1[j];
                 }
                 for (int i = k + 2 + threadIdx.x; i < n; i += NT) {
                     S[(size_t)i * lds + k] = l0[i];

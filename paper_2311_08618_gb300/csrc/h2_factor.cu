@@ -483,14 +483,14 @@ __global__ void __launch_bounds__(NT) k_trsm(FactorArgs A, int use_smem) {
         const double* wi = W + (size_t)i * D;
         double v;
         if (spiv[j] == 1) {
-            v = wi[j] / sL[(size_t)j * ldl + j];
+            v = wi[j] * (1.0 / sL[(size_t)j * ldl + j]);
         } else {
             int j0 = spiv[j] == 2 ? j : j - 1;
             double a0 = sL[(size_t)j0 * ldl + j0], b0 = sL[(size_t)(j0 + 1) * ldl + j0],
                    c0 = sL[(size_t)(j0 + 1) * ldl + j0 + 1];
-            double det = a0 * c0 - b0 * b0;
+            double idet = 1.0 / (a0 * c0 - b0 * b0);
             double w0 = wi[j0], w1 = wi[j0 + 1];
-            v = (j == j0) ? (w0 * c0 - w1 * b0) / det : (w1 * a0 - w0 * b0) / det;
+            v = (j == j0) ? (w0 * c0 - w1 * b0) * idet : (w1 * a0 - w0 * b0) * idet;
         }
         Y[(size_t)i * D + j] = v;
     }
