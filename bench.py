@@ -41,8 +41,25 @@ import numpy as np  # noqa: E402
 
 import workloads as W  # noqa: E402
 
-WORKLOAD = dict(name="laplace2d_n1024", n=1024, d=2, seed=1, kernel=W.LAPLACE_EPS,
-                kparams=(1e-3, 0.0, 0.0, 0.0), leaf=64, rank=16, eta=1.0, k=512, tol=1e-8)
+WORKLOADS = {
+    # the default bench workload: n = 1024 uniform in the unit square, 1/(r+1e-3)
+    "laplace2d_n1024": dict(name="laplace2d_n1024", n=1024, d=2, seed=1, kernel=W.LAPLACE_EPS,
+                            kparams=(1e-3, 0.0, 0.0, 0.0), leaf=64, rank=16, eta=1.0, k=512, tol=1e-8),
+    # the precision configuration: cylindrical lattice (radius 5, spacing 0.14,
+    # jitter 0.01), exp(-r^2/2) + 1e-2/(r + 0.1), leaf 256, rank 48
+    "cylinder_n262144": dict(name="cylinder_n262144", n=262144, d=3, seed=4, kernel=W.GAUSS_PLUS_INV,
+                             kparams=(1e-2, 0.1, 0.0, 0.0), leaf=256, rank=48, eta=1.0, k=131072, tol=1e-8),
+    # the 3D Yukawa configuration: n = 65536 uniform in the unit cube
+    "yukawa3d_n65536": dict(name="yukawa3d_n65536", n=65536, d=3, seed=2, kernel=W.YUKAWA_EPS,
+                            kparams=(1e-3, 0.0, 0.0, 0.0), leaf=256, rank=32, eta=1.0, k=32768, tol=1e-8),
+}
+WORKLOAD = WORKLOADS["laplace2d_n1024"]
+
+
+def _points(wl):
+    if wl["name"].startswith("cylinder"):
+        return W.cylinder_lattice(wl["n"], wl["seed"])
+    return W.uniform_cube(wl["n"], wl["d"], wl["seed"])
 METRIC = "LDL-inertia shifts/sec (FP64); k-th eigs/sec at tol 1e-8 with p50/p99"
 FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 (profiling recipe table); not in MEASURED_PEAKS
 # DRAM traffic of one k_schur launch from the committed ncu capture, valid while
@@ -240,13 +257,33 @@ def ours(args, rank, world, local, dist):
         _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream)
 
 
+def _finish_short(args, rank, world, M, info, value, e2e_value, lanes, ms_max, clocks, build_s, same):
+    """Line for a workload measured without the k-th solves (large configurations)."""
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "shifts/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD["name"], "n": WORKLOAD["n"], "leaf": WORKLOAD["leaf"],
+                           "rank": WORKLOAD["rank"], "eta": WORKLOAD["eta"], "shifts_per_step": lanes,
+                           "precision": ["fp64", "mixed"][args.precision],
+                           "workspace_gb": info["workspace_bytes"] / 1e9},
+                "e2e": {"value": e2e_value, "unit": "shifts/s", "h2d_bytes_per_step": 8 * lanes,
+                        "d2h_bytes_per_step": 8 * lanes, "counts_match_device_path": same},
+                "gpu_launches": info["kernels_per_batch"] * args.steps, "build_s": build_s, "clocks": clocks,
+                "info": {k: info[k] for k in ("levels", "leaves", "max_rank", "near_pairs", "fill_pairs",
+                                              "norm_inf", "kernels_per_batch")}}
+        print(json.dumps(line), flush=True)
+    M.close()
+
+
 def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
     import torch
     lanes = args.lanes
-    X = W.uniform_cube(WORKLOAD["n"], WORKLOAD["d"], WORKLOAD["seed"])
+    X = _points(WORKLOAD)
     t0 = time.time()
     M = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
-                     eta=WORKLOAD["eta"], max_lanes=lanes, stream=stream.cuda_stream)
+                     eta=WORKLOAD["eta"], max_lanes=lanes, stream=stream.cuda_stream, precision=args.precision)
     torch.cuda.synchronize()
     build_s = time.time() - t0
     info = M.h2_info()
@@ -303,6 +340,8 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
     info = M.h2_info()
     # ---- k-th eigenvalue solves (all of the path incl. the bisection driver),
     # on a handle with eig_lanes lanes (latency: fewer lanes per round)
+    if args.eig_solves <= 0:
+        return _finish_short(args, rank, world, M, info, value, e2e_value, lanes, ms_max, clocks, build_s, same)
     Me = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
                       eta=WORKLOAD["eta"], max_lanes=args.eig_lanes, stream=stream.cuda_stream)
     lat = []
@@ -473,9 +512,13 @@ def main():
     ap.add_argument("--serving-s", type=float, default=3.0, help="seconds of arrivals (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=40.0)
     ap.add_argument("--serving-lanes", type=int, default=16)
+    ap.add_argument("--workload", default="laplace2d_n1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1], help="0 FP64, 1 mixed (main handle)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    global WORKLOAD
+    WORKLOAD = WORKLOADS[args.workload]
     rank, world, local, dist = _dist()
     try:
         if args.impl == "reference":
