@@ -62,9 +62,13 @@ def _points(wl):
     return W.uniform_cube(wl["n"], wl["d"], wl["seed"])
 METRIC = "LDL-inertia shifts/sec (FP64); k-th eigs/sec at tol 1e-8 with p50/p99"
 FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 (profiling recipe table); not in MEASURED_PEAKS
-# DRAM traffic of one k_schur launch from the committed ncu capture, valid while
-# the factorization source is unchanged (sha256 prefix recorded with it)
-NCU_TRAFFIC = {"kernel": "k_schur", "bytes_per_launch": None, "source_sha": None}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per k_schur launch,
+# the mean over the 31 launches of one batch, from the ncu capture summarised in
+# profiles/k_schur_laplace2d_n1024_256lanes.md; valid for that workload and lane
+# count while the kernel's source is unchanged (sha256 prefix of its text)
+NCU_TRAFFIC = {"kernel": "k_schur", "workload": "laplace2d_n1024", "lanes": 256,
+               "bytes_per_launch": 327.2e6, "source_sha": "5a1bc59e734badc5"}
+KERNEL_REGIONS = {"k_schur": ("h2_factor.cu", "struct SchurArgs {", "// leaf level: copy")}
 
 
 def _peaks():
@@ -75,12 +79,18 @@ def _peaks():
         return {}
 
 
-def _source_sha():
-    h = hashlib.sha256()
-    for f in ("h2_factor.cu", "h2_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2311_08618_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+def _kernel_sha(kernel):
+    """sha256 prefix of a kernel's source text (None if it cannot be located)."""
+    if kernel not in KERNEL_REGIONS:
+        return None
+    f, start, end = KERNEL_REGIONS[kernel]
+    with open(os.path.join(ROOT, "paper_2311_08618_gb300", "csrc", f)) as fh:
+        src = fh.read()
+    a = src.find(start)
+    b = src.find(end, a + 1)
+    if a < 0 or b < 0:
+        return None
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
 def _shift_batches(lo, hi, lanes, count, seed=7):
@@ -314,6 +324,7 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
     ms = e0.elapsed_time(e1)
     ms_max = _max_over_ranks(ms, dist, dev)
     value = world * args.steps * lanes / (ms_max / 1e3)
+    cnt_fp64 = d_cnt.clone()          # FP64 counts (the buffers are reused below)
     # ---- end to end: host (pinned) shifts in, host counts out, every step
     h_sh = torch.tensor(sh, dtype=torch.float64).pin_memory()
     h_cnt = torch.zeros((total, lanes), dtype=torch.int64).pin_memory()
@@ -386,7 +397,8 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
                 "peak_source": "measured hbm_gbs"}
     traffic = None
     if NCU_TRAFFIC["bytes_per_launch"] and NCU_TRAFFIC["kernel"] == "k_" + dom and \
-            NCU_TRAFFIC["source_sha"] == _source_sha():
+            NCU_TRAFFIC["workload"] == WORKLOAD["name"] and NCU_TRAFFIC["lanes"] == lanes and \
+            NCU_TRAFFIC["source_sha"] == _kernel_sha(NCU_TRAFFIC["kernel"]):
         traffic = NCU_TRAFFIC["bytes_per_launch"]
     roof.update({"kernel": "k_" + dom, "traffic": traffic, "flops_per_launch": flops_launch,
                  "bytes_per_launch": bytes_launch, "launch_ms": per_launch_ms,
@@ -424,6 +436,29 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
                  "mixed_rounds": infm["last_mixed_rounds"], "bracket_resets": infm["bracket_resets"],
                  "lambda": float(outm[0]), "abs_diff_vs_fp64": float(abs(outm[0] - lam[0]))}
     Mx.close()
+    # ---- the plain FP64 path: one shift per launch sequence (1 lane), kernels
+    # launched one by one (no graph, no batching)
+    Mp = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
+                      eta=WORKLOAD["eta"], max_lanes=1, stream=stream.cuda_stream, graphs=0)
+    nplain = min(64, lanes)
+    p_cnt = torch.zeros(nplain, dtype=torch.int64, device=dev)
+    src = d_sh[args.warmup]
+    for j in range(3):
+        Mp.h2_inertia_device(src[j:j + 1], 1, p_cnt[j:j + 1])
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for j in range(nplain):
+        Mp.h2_inertia_device(src[j:j + 1], 1, p_cnt[j:j + 1])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    plain_rate = nplain / (ms_plain / 1e3)
+    plain_same = bool(torch.equal(p_cnt, cnt_fp64[args.warmup][:nplain]))
+    Mp.close()
+    plain = {"mode": "FP64, 1 lane, kernels launched one by one (no graph, no batching)", "value": plain_rate,
+             "unit": "shifts/s", "shifts": nplain, "counts_equal_to_batched": plain_same,
+             "batched_fp64_over_plain": value / plain_rate,
+             "batched_mixed_over_plain": precision["value"] / plain_rate}
     serving_res = _serving(args) if args.serving_s > 0 and world == 1 else None
     ws_mb = info["workspace_bytes"] / 1e6
     line = {"metric": METRIC, "value": value, "unit": "shifts/s", "n_gpus": world, "steps": args.steps,
@@ -442,12 +477,12 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
                      "rounds": info2["last_rounds"], "shifts_per_solve": info2["last_shifts"],
                      "lambda": lam[0], "err_bound": lam[1]},
             "build_s": build_s, "roofline": roof, "clocks": clocks, "precision": precision,
-            "serving": serving_res}
+            "plain_fp64": plain, "serving": serving_res}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         sample = list(sh[args.warmup][:: max(1, lanes // (2 * cores))][:2 * cores])
         rate, secs, ocounts = oracle_throughput(sample, cores)
-        got = {s: int(c) for s, c in zip(sh[args.warmup], d_cnt[args.warmup].cpu().numpy())}
+        got = {s: int(c) for s, c in zip(sh[args.warmup], cnt_fp64[args.warmup].cpu().numpy())}
         agree = sum(int(got[s] == ocounts[s]) for s in sample)
         line["cpu_baseline"] = {"value": rate, "unit": "shifts/s", "cores": cores, "kind": "oracle",
                                 "sample": "%d shifts of step 1 (%.1f s wall, one process per core)" %
@@ -461,22 +496,20 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
 SERVING_SIZES = (1024, 2048, 4096, 8192)
 
 
-def _serving(args):
-    """Open-loop serving: Poisson arrivals of k-th eigenvalue queries (k uniform,
-    tol log-uniform in [1e-10, 1e-6]) over resident 2D Laplace H^2 matrices of
-    different sizes; continuous batching (paper_2311_08618_gb300.serving)."""
+def _serving_run(args, rate, seconds, seed):
+    """One open-loop run on freshly built resident matrices (cold (mu, nu)
+    tables): Poisson arrivals at `rate` for `seconds`."""
     from paper_2311_08618_gb300 import serving
     srv = serving.Server()
     for i, n in enumerate(SERVING_SIZES):
         srv.add_matrix("m%d" % i, W.uniform_cube(n, 2, 100 + i), W.LAPLACE_EPS, (1e-3, 0, 0, 0), 64, 16,
                        lanes=args.serving_lanes)
-    rate = args.serving_rate
-    u = W.uniform(4242, 4 * 100000)
+    u = W.uniform(seed, 4 * 100000)
     arr, t, j = [], 0.0, 0
     while True:
         t += -math.log(1.0 - u[j]) / rate
         j += 1
-        if t > args.serving_s:
+        if t > seconds:
             break
         mi = int(u[j] * len(SERVING_SIZES))
         k = 1 + int(u[j + 1] * SERVING_SIZES[mi])
@@ -484,18 +517,28 @@ def _serving(args):
         j += 3
         arr.append((t, "m%d" % mi, k, tol))
     t0 = time.perf_counter()
-    done, unfinished = serving.run_open_loop(srv, arr, args.serving_s, deadline_s=args.serving_s + 25.0)
+    done, unfinished = serving.run_open_loop(srv, arr, seconds, deadline_s=seconds + 25.0)
     wall = time.perf_counter() - t0
-    st = serving.latency_stats(done)
-    res = {"matrices": "4 resident 2D Laplace H2 matrices n=%s (leaf 64, rank 16), %d lanes each"
-                       % (list(SERVING_SIZES), args.serving_lanes),
-           "stand_in": "the 64-matrix 3D n<=131072 configuration needs ~16-70 GB per lane under eta=1 box "
-                       "admissibility and does not fit one GPU",
-           "arrivals": "Poisson %.0f q/s for %.0f s" % (rate, args.serving_s), "offered": len(arr),
+    res = {"arrivals": "Poisson %.0f q/s for %.0f s" % (rate, seconds), "offered": len(arr),
            "completed": len(done), "unfinished": unfinished, "wall_s": wall,
            "eigs_per_s": len(done) / wall, "shifts_per_s": srv.shifts_evaluated / wall, "ticks": srv.ticks}
-    res.update(st)
+    res.update(serving.latency_stats(done))
     srv.close()
+    return res
+
+
+def _serving(args):
+    """Open-loop serving: Poisson arrivals of k-th eigenvalue queries (k uniform,
+    tol log-uniform in [1e-10, 1e-6]) over resident 2D Laplace H^2 matrices of
+    different sizes; continuous batching (paper_2311_08618_gb300.serving).  One
+    run at the offered (overload) rate and one at a sustainable rate."""
+    res = {"matrices": "4 resident 2D Laplace H2 matrices n=%s (leaf 64, rank 16), %d lanes each, FP64"
+                       % (list(SERVING_SIZES), args.serving_lanes),
+           "stand_in": "the 64-matrix 3D n<=131072 configuration needs ~16-70 GB per lane under eta=1 box "
+                       "admissibility and does not fit one GPU"}
+    res.update(_serving_run(args, args.serving_rate, args.serving_s, 4242))
+    if args.serving_sustain_rate > 0:
+        res["sustainable"] = _serving_run(args, args.serving_sustain_rate, args.serving_sustain_s, 4343)
     return res
 
 
@@ -511,6 +554,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-s", type=float, default=3.0, help="seconds of arrivals (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=40.0)
+    ap.add_argument("--serving-sustain-rate", type=float, default=2.0, help="second, sustainable rate (0: skip)")
+    ap.add_argument("--serving-sustain-s", type=float, default=5.0)
     ap.add_argument("--serving-lanes", type=int, default=16)
     ap.add_argument("--workload", default="laplace2d_n1024", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1], help="0 FP64, 1 mixed (main handle)")

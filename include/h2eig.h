@@ -82,6 +82,13 @@ typedef struct {
                             pivot_guard * ||A||_inf is re-run in FP64; 0 = 1e-4 */
     void* stream;        /* cudaStream_t for all work of the handle; NULL = a
                             stream created by the library */
+    int graphs;          /* 1 (default): each batch replays a CUDA graph
+                            captured at build; 0: the batch's kernels are
+                            launched one by one (the plain launch path) */
+    int recomp_cluster_cols; /* fill recompression of a level whose Z (the
+                            redundant rows of all fill blocks of a row, Sec.
+                            3.4) may reach this many columns runs on a cluster
+                            of 8 CTAs; 0 = 4096, < 0 = never */
 } h2_options;
 
 /* Fills *opt with the defaults above.  Never fails. */

@@ -30,7 +30,8 @@ class Kernel(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("admissibility", C.c_int), ("eps_h2", C.c_double),
                 ("fill_cap", C.c_int), ("sketch_cols", C.c_int), ("seed", C.c_uint64),
-                ("max_lanes", C.c_int), ("pivot_guard", C.c_double), ("stream", C.c_void_p)]
+                ("max_lanes", C.c_int), ("pivot_guard", C.c_double), ("stream", C.c_void_p),
+                ("graphs", C.c_int), ("recomp_cluster_cols", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -41,6 +41,7 @@ void h2_default_options(h2_options* opt) {
     opt->max_lanes = 64;
     opt->pivot_guard = 1e-4;
     opt->stream = nullptr;
+    opt->graphs = 1;
 }
 
 const char* h2_last_error(void) { return g_last_error.c_str(); }

@@ -151,7 +151,6 @@ __global__ void k_basis(const double* Ylev, int s, const int64_t* off, int leaf_
     int c = blockIdx.x;
     __shared__ double red[32];
     __shared__ int redi[32];
-    extern __shared__ double colnorm[];
     double* Yh = scratch + (size_t)c * ((size_t)dq * s + (size_t)dq * dq);
     double* V = Yh + (size_t)dq * s;
     int64_t r0 = off[c];
@@ -176,7 +175,7 @@ __global__ void k_basis(const double* Ylev, int s, const int64_t* off, int leaf_
         }
     }
     __syncthreads();
-    int k = cta_pivqr<NT>(Yh, s, m, s, tol, cap, V, dq, colnorm, red, redi);
+    int k = cta_pivqr<NT>(Yh, s, m, s, tol, cap, V, dq, red, redi);
     double* Q = Qout + (size_t)c * dq * dq;
     cta_form_q<NT>(Q, dq, m, V, dq, k);
     if (threadIdx.x == 0) rank_out[c] = k;
@@ -382,7 +381,7 @@ int build_device(h2_matrix* h) {
         if ((rc = dalloc(&d_scr, (size_t)D.nc * ((size_t)D.dq * s + (size_t)D.dq * D.dq)))) return rc;
         if ((rc = dalloc(&D.d_Q, (size_t)D.nc * D.dq * D.dq))) return rc;
         if ((rc = dalloc(&D.d_rb, D.nc))) return rc;
-        k_basis<<<D.nc, NT, s * sizeof(double), st>>>(d_Y, s, d_off, leaf_level,
+        k_basis<<<D.nc, NT, 0, st>>>(d_Y, s, d_off, leaf_level,
                                                        leaf_level ? nullptr : d_E[l + 1], rbc,
                                                        leaf_level ? nullptr : h->lev[l + 1].d_rb, D.dq,
                                                        h->tol, cap, d_scr, D.d_Q, D.d_rb);

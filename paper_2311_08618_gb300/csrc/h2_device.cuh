@@ -143,30 +143,33 @@ __device__ __forceinline__ double block_sum1(double v, double* buf, int par) {
 // dimension ldy), in place, stopped when the Frobenius norm of the
 // not-yet-pivoted remainder Y[k:, k:] is <= tol, or after `cap` steps.
 // Reflector k is stored in V (row-major m x ldv, column k, rows k..m-1,
-// unit 2-norm; a zero vector means H_k = I).  colnorm: scratch of s doubles.
-// Returns k (the rank).  All threads of the CTA call it.
+// unit 2-norm; a zero vector means H_k = I).  Returns k (the rank).  All
+// threads of the CTA call it.
+//
+// The column norms of step k+1 are recomputed exactly (no downdating), in the
+// same pass that applies reflector k: the sum over rows k+1..m-1 of the
+// updated column, in row order.  The pivot column k itself is not updated (it
+// is never read again: only the reflectors are used).  Pivot: the largest
+// norm, the smallest column index among equal norms.
 template <int NT>
 __device__ int cta_pivqr(double* Y, int ldy, int m, int s, double tol, int cap, double* V,
-                         int ldv, double* colnorm, double* red, int* redi, int* bad = nullptr) {
+                         int ldv, double* red, int* redi, int* bad = nullptr) {
     // red / redi: at least 2 * NT / 32 entries (double-buffered reductions)
     int kmax = min(min(m, s), cap);
     int k = 0;
     int par = 0;
-    for (; k < kmax; ++k) {
-        // trailing column norms (exact recomputation, no downdating); each
-        // thread owns its columns, so no barrier is needed before the scan
-        double part = 0.0, best = -1.0;
-        int bi = 0x7fffffff;
-        for (int j = k + threadIdx.x; j < s; j += NT) {
-            double a = 0.0;
-            for (int i = k; i < m; ++i) {
-                double y = Y[(size_t)i * ldy + j];
-                a += y * y;
-            }
-            colnorm[j] = a;
-            part += a;
-            if (a > best) { best = a; bi = j; }
+    double part = 0.0, best = -1.0;
+    int bi = 0x7fffffff;
+    for (int j = threadIdx.x; j < s; j += NT) {        // norms of step 0
+        double a = 0.0;
+        for (int i = 0; i < m; ++i) {
+            double y = Y[(size_t)i * ldy + j];
+            a += y * y;
         }
+        part += a;
+        if (a > best) { best = a; bi = j; }
+    }
+    for (; k < kmax; ++k) {
         double total = block_sum1<NT>(part, red, par);
         par ^= 1;
         if (!(total == total)) {          // NaN input: stop, report, touch nothing
@@ -212,14 +215,30 @@ __device__ int cta_pivqr(double* Y, int ldy, int m, int s, double tol, int cap, 
             V[(size_t)i * ldv + k] = x;
         }
         __syncthreads();
-        if (nv > 0.0) {
-            // Y[k:, j] -= 2 v (v . Y[k:, j]) for j >= k
-            for (int j = k + threadIdx.x; j < s; j += NT) {
+        // Y[k:, j] -= 2 v (v . Y[k:, j]) for j > k, and the norms of step k+1
+        part = 0.0;
+        best = -1.0;
+        bi = 0x7fffffff;
+        for (int j = k + 1 + threadIdx.x; j < s; j += NT) {
+            double a = 0.0;
+            if (nv > 0.0) {
                 double w = 0.0;
                 for (int i = k; i < m; ++i) w += V[(size_t)i * ldv + k] * Y[(size_t)i * ldy + j];
                 w *= 2.0;
-                for (int i = k; i < m; ++i) Y[(size_t)i * ldy + j] -= w * V[(size_t)i * ldv + k];
+                Y[(size_t)k * ldy + j] -= w * V[(size_t)k * ldv + k];
+                for (int i = k + 1; i < m; ++i) {
+                    double y = Y[(size_t)i * ldy + j] - w * V[(size_t)i * ldv + k];
+                    Y[(size_t)i * ldy + j] = y;
+                    a += y * y;
+                }
+            } else {
+                for (int i = k + 1; i < m; ++i) {
+                    double y = Y[(size_t)i * ldy + j];
+                    a += y * y;
+                }
             }
+            part += a;
+            if (a > best) { best = a; bi = j; }
         }
         __syncthreads();
     }

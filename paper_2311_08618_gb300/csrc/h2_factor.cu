@@ -24,6 +24,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "h2_device.cuh"
 #include "h2_internal.h"
 
@@ -83,7 +85,7 @@ struct HbScope {
 
 // scratch layout of one elimination (offsets in doubles)
 struct ScratchLayout {
-    size_t z, colnorm, vr, vq, tmp, f, iperm, hdr, w, y, total;
+    size_t z, vr, vq, tmp, f, iperm, hdr, w, y, total;
 };
 
 static ScratchLayout scratch_layout(int D, int nfill_max, int ntarg_max) {
@@ -91,7 +93,6 @@ static ScratchLayout scratch_layout(int D, int nfill_max, int ntarg_max) {
     size_t zcols = (size_t)std::max(nfill_max, 1) * D;
     size_t o = 0;
     s.z = o; o += (size_t)D * zcols;
-    s.colnorm = o; o += zcols;
     s.vr = o; o += (size_t)D * D;
     s.vq = o; o += (size_t)D * D;
     s.tmp = o; o += (size_t)D * D;
@@ -191,7 +192,6 @@ __global__ void __launch_bounds__(NT) k_recomp(FactorArgs A) {
     const int m = A.dim[p * LN + lane], r0 = A.rk[p * LN + lane];
     double* scr = A.scratch + ((size_t)ci * LN + lane) * A.lay.total;
     double* Z = scr + A.lay.z;
-    double* colnorm = scr + A.lay.colnorm;
     double* Vr = scr + A.lay.vr;
     double* Vq = scr + A.lay.vq;
     int* hdr = (int*)(scr + A.lay.hdr);
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(NT) k_recomp(FactorArgs A) {
         }
         __syncthreads();
         int capt = max(0, min(A.fill_cap, m) - r0);
-        t = cta_pivqr<NT>(Z, wz, R, wz, A.tol, capt, Vr, D, colnorm, red, redi, &s_bad);
+        t = cta_pivqr<NT>(Z, wz, R, wz, A.tol, capt, Vr, D, red, redi, &s_bad);
         if (t > 0) cta_form_q<NT>(Vq, D, R, Vr, D, t);
         if (threadIdx.x == 0)
             add_stats(A.stats, H2_KIND_RECOMP, 4.0 * R * (double)wz * t + 4.0 * (double)R * R * t,
@@ -245,11 +245,374 @@ __global__ void __launch_bounds__(NT) k_recomp(FactorArgs A) {
     }
 }
 
+// ---- (i') the same recompression for wide fill rows: one thread-block
+// cluster of QG CTAs per (cluster, lane).  The columns of Z are split into QG
+// contiguous ranges; per step the CTAs exchange their partial norm sums and
+// pivot candidates through distributed shared memory, CTA 0 swaps the pivot
+// column into place, and every CTA forms the same reflector from it and
+// applies it to its own columns (fusing the norms of the next step, as
+// cta_pivqr does).  The pivot rule (largest norm, then smallest index) does
+// not depend on the split, so the reflectors equal those of cta_pivqr; only
+// the addition order of the stopping sum differs.
+namespace cg = cooperative_groups;
+constexpr int QG = 8;
+struct QPart {
+    double total, best;
+    int bi, pad;
+};
+
+__device__ int cluster_pivqr(cg::cluster_group& cl, int g, double* Y, int ldy, int m, int s, double tol, int cap,
+                             double* V, int ldv, double* sv, double* red, int* redi, QPart* xs, int* bad) {
+    const int cw = (s + QG - 1) / QG;
+    const int jlo = g * cw, jhi = min(s, jlo + cw);
+    const int kmax = min(min(m, s), cap);
+    int par = 0, xp = 0, k = 0;
+    double part = 0.0, best = -1.0;
+    int bi = 0x7fffffff;
+    for (int j = jlo + threadIdx.x; j < jhi; j += NT) {   // norms of step 0
+        double a = 0.0;
+        for (int i = 0; i < m; ++i) {
+            double y = Y[(size_t)i * ldy + j];
+            a += y * y;
+        }
+        part += a;
+        if (a > best) { best = a; bi = j; }
+    }
+    for (; k < kmax; ++k) {
+        const double ctot = block_sum1<NT>(part, red, par);
+        par ^= 1;
+        double cbv;
+        const int cbi = block_argmax1<NT>(best, bi, red, redi, par, &cbv);
+        par ^= 1;
+        if (threadIdx.x == 0) {
+            xs[xp].total = ctot;
+            xs[xp].best = cbv;
+            xs[xp].bi = cbi;
+        }
+        cl.sync();
+        double total = 0.0, bv = -1.0;
+        int jp = 0x7fffffff;
+        for (int r = 0; r < QG; ++r) {       // the same order on every CTA
+            const QPart* q = cl.map_shared_rank(&xs[xp], r);
+            total += q->total;
+            if (q->best > bv || (q->best == bv && q->bi < jp)) { bv = q->best; jp = q->bi; }
+        }
+        xp ^= 1;
+        if (!(total == total)) {
+            if (bad && threadIdx.x == 0 && g == 0) *bad = 1;
+            break;
+        }
+        if (sqrt(total) <= tol) break;
+        if (jp < k || jp >= s) jp = k;
+        if (g == 0 && jp != k)
+            for (int i = threadIdx.x; i < m; i += NT) {
+                double t = Y[(size_t)i * ldy + k];
+                Y[(size_t)i * ldy + k] = Y[(size_t)i * ldy + jp];
+                Y[(size_t)i * ldy + jp] = t;
+            }
+        cl.sync();
+        // reflector from x = Y[k:, k], identical on every CTA
+        double nx2 = 0.0;
+        for (int i = k + threadIdx.x; i < m; i += NT) {
+            double x = Y[(size_t)i * ldy + k];
+            nx2 += x * x;
+        }
+        nx2 = block_sum1<NT>(nx2, red, par);
+        par ^= 1;
+        const double nx = sqrt(nx2);
+        const double x0 = Y[(size_t)k * ldy + k];
+        const double alpha = x0 >= 0.0 ? -nx : nx;
+        const double v0 = x0 - alpha;
+        double nv2 = 0.0;
+        for (int i = k + threadIdx.x; i < m; i += NT) {
+            double x = (i == k) ? v0 : Y[(size_t)i * ldy + k];
+            nv2 += x * x;
+        }
+        nv2 = block_sum1<NT>(nv2, red, par);
+        par ^= 1;
+        const double nv = sqrt(nv2);
+        for (int i = threadIdx.x; i < m; i += NT) {
+            double x = 0.0;
+            if (i >= k && nv > 0.0) x = ((i == k) ? v0 : Y[(size_t)i * ldy + k]) / nv;
+            sv[i] = x;
+            if (g == 0) V[(size_t)i * ldv + k] = x;
+        }
+        __syncthreads();
+        // own columns j > k: apply the reflector, norms of step k+1
+        part = 0.0;
+        best = -1.0;
+        bi = 0x7fffffff;
+        for (int j = max(jlo, k + 1) + threadIdx.x; j < jhi; j += NT) {
+            double a = 0.0;
+            if (nv > 0.0) {
+                double w = 0.0;
+                for (int i = k; i < m; ++i) w += sv[i] * Y[(size_t)i * ldy + j];
+                w *= 2.0;
+                Y[(size_t)k * ldy + j] -= w * sv[k];
+                for (int i = k + 1; i < m; ++i) {
+                    double y = Y[(size_t)i * ldy + j] - w * sv[i];
+                    Y[(size_t)i * ldy + j] = y;
+                    a += y * y;
+                }
+            } else {
+                for (int i = k + 1; i < m; ++i) {
+                    double y = Y[(size_t)i * ldy + j];
+                    a += y * y;
+                }
+            }
+            part += a;
+            if (a > best) { best = a; bi = j; }
+        }
+        __syncthreads();
+    }
+    cl.sync();     // V complete; no CTA leaves while others read its xs
+    return k;
+}
+
+__global__ void __cluster_dims__(QG, 1, 1) __launch_bounds__(NT) k_recomp_cluster(FactorArgs A) {
+    HbScope hb_(1);
+    cg::cluster_group cl = cg::this_cluster();
+    const int g = (int)cl.block_rank();
+    const int ci = blockIdx.x / QG, lane = blockIdx.y;
+    // every early return below depends on (ci, lane) only: taken by the whole cluster
+    if (lane >= *A.active) return;
+    extern __shared__ double sv[];       // reflector, D doubles
+    __shared__ double red[2 * NT / 32];
+    __shared__ int redi[2 * NT / 32];
+    __shared__ QPart xs[2];
+    __shared__ int s_bad;
+    const int D = A.D, LN = A.lanes;
+    const int p = A.cl[ci];
+    const int m = A.dim[p * LN + lane], r0 = A.rk[p * LN + lane];
+    double* scr = A.scratch + ((size_t)ci * LN + lane) * A.lay.total;
+    double* Z = scr + A.lay.z;
+    double* Vr = scr + A.lay.vr;
+    double* Vq = scr + A.lay.vq;
+    int* hdr = (int*)(scr + A.lay.hdr);
+    const int R = m - r0;
+    const int nf = A.nfill[ci];
+    if (m < 0 || m > D || r0 < 0 || r0 > m || nf < 0 || nf > A.nfill_max) {
+        if (g == 0 && threadIdx.x == 0) report_bad(A.err, 1, m, r0, nf, D);
+        return;
+    }
+    int wz = 0, badq = -1;
+    for (int f = 0; f < nf; ++f) {
+        int lq = live_rows(A, A.fillq[ci * A.nfill_max + f], lane);
+        if (lq < 0 || lq > D) badq = lq;
+        wz += lq;
+    }
+    if (badq != -1) {
+        if (g == 0 && threadIdx.x == 0) report_bad(A.err, 1, badq, wz, m, D);
+        return;
+    }
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    int t = 0;
+    const int run = (nf > 0 && R > 0) ? 1 : 0;
+    if (run) {
+        // Z = rows r0.. of every fill block of row p, assembled by the cluster
+        int coff = 0;
+        for (int f = 0; f < nf; ++f) {
+            int q = A.fillq[ci * A.nfill_max + f];
+            int lq = live_rows(A, q, lane);
+            double* B = slot_ptr(A.slots, A.fillslot[ci * A.nfill_max + f], LN, lane, D);
+            int tr = p > q ? 0 : 1;
+            for (int e = g * NT + threadIdx.x; e < R * lq; e += QG * NT) {
+                int i = e / lq, j = e % lq;
+                Z[(size_t)i * wz + coff + j] = belem(B, D, tr, r0 + i, j);
+            }
+            coff += lq;
+        }
+        cl.sync();
+        int capt = max(0, min(A.fill_cap, m) - r0);
+        t = cluster_pivqr(cl, g, Z, wz, R, wz, A.tol, capt, Vr, D, sv, red, redi, xs, &s_bad);
+        if (g == 0) {
+            if (t > 0) cta_form_q<NT>(Vq, D, R, Vr, D, t);
+            if (threadIdx.x == 0)
+                add_stats(A.stats, H2_KIND_RECOMP, 4.0 * R * (double)wz * t + 4.0 * (double)R * R * t,
+                          8.0 * 2.0 * R * (double)wz);
+        }
+    }
+    if (g == 0 && threadIdx.x == 0) {
+        hdr[2] = r0;
+        hdr[3] = t;
+        hdr[4] = run;
+        A.rk[p * LN + lane] = r0 + t;
+        if (s_bad) atomicOr(A.err, 1);
+    }
+}
+
 // ---- (ii) rotation of p's redundant coordinates in one block of row p and
 // truncation of a fill-in block: one CTA per (row block, cluster, lane)
-constexpr int RC = 32;   // column (or row) chunk staged in shared memory
+constexpr int RC = 32;   // columns (or rows) of the block rotated per pass
+constexpr int RK = 32;   // rows of V staged in shared memory per step
+
+// VEC consecutive T values from shared memory (VEC * sizeof(T)-byte aligned)
+__device__ __forceinline__ void ldsv(const float* p, float (&v)[2]) {
+    float2 q = *reinterpret_cast<const float2*>(p);
+    v[0] = q.x; v[1] = q.y;
+}
+__device__ __forceinline__ void ldsv(const double* p, double (&v)[1]) { v[0] = *p; }
+
+// out(i, c) = sum_k V[k][ib + i] * slab[k][c] for the column c = tx and the
+// rows i = VEC*ty + 8*VEC*g + u (u < VEC, g < ng) of one pass over up to 8*NU
+// rows starting at ib; V is the R x R rotation in global memory (leading
+// dimension D), staged RK rows at a time in vs (leading dimension 8*NU) in the
+// product type T.  VEC = 2 for float (pairs of rows per load), 1 for double;
+// ng = the row groups this pass needs, so no padded rows are computed beyond
+// the last group of 8*VEC rows.
+template <typename T, int NU>
+__device__ __forceinline__ void rot_product(const T* slab, T* vs, const double* V, int D, int R, int ib,
+                                            T (&acc)[NU]) {
+    constexpr int VEC = sizeof(T) == 4 ? 2 : 1;
+    constexpr int LDV = 8 * NU;
+    constexpr int G = NU / VEC;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+    const int ng = min(G, (R - ib + 8 * VEC - 1) / (8 * VEC));
+#pragma unroll
+    for (int u = 0; u < NU; ++u) acc[u] = (T)0;
+    for (int k0 = 0; k0 < R; k0 += RK) {
+        const int kc = min(RK, R - k0);
+        for (int e = threadIdx.x; e < RK * LDV; e += NT) {
+            int k = e / LDV, i = e % LDV;
+            vs[e] = (k < kc && ib + i < R) ? (T)V[(size_t)(k0 + k) * D + ib + i] : (T)0;
+        }
+        __syncthreads();
+        for (int k = 0; k < kc; ++k) {
+            const T y = slab[(k0 + k) * RC + tx];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (g < ng) {
+                    T v[VEC];
+                    ldsv(vs + k * LDV + 8 * VEC * g + VEC * ty, v);
+#pragma unroll
+                    for (int u = 0; u < VEC; ++u) acc[VEC * g + u] += v[u] * y;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// row of pass-local output u of this thread (see rot_product)
 template <typename T>
+__device__ __forceinline__ int rot_row(int u) {
+    constexpr int VEC = sizeof(T) == 4 ? 2 : 1;
+    return VEC * (threadIdx.x / 32) + 8 * VEC * (u / VEC) + u % VEC;
+}
+
+// Rotates rows r0.. of block B (row side) or its columns r0.. (column side of
+// the diagonal block) by V, in passes of RC columns (rows) staged in slab.
+template <typename T, int NU>
+__device__ void rotate_block(double* B, int D, int tr, int r0, int R, int dx, int m, const double* V, T* slab,
+                             T* vs) {
+    const int tx = threadIdx.x % 32;
+    T acc[NU];
+    // row side: rows r0.. of p, over the dx live columns of x
+    for (int j0 = 0; j0 < dx; j0 += RC) {
+        const int nj = min(RC, dx - j0);
+        for (int e = threadIdx.x; e < R * RC; e += NT) {
+            int k, j;
+            if (tr) { j = e / R; k = e % R; } else { k = e / RC; j = e % RC; }
+            slab[k * RC + j] = j < nj ? (T)belem(B, D, tr, r0 + k, j0 + j) : (T)0;
+        }
+        __syncthreads();
+        for (int ib = 0; ib < R; ib += 8 * NU) {
+            rot_product<T, NU>(slab, vs, V, D, R, ib, acc);
+            if (tx < nj) {
+#pragma unroll
+                for (int u = 0; u < NU; ++u) {
+                    int i = ib + rot_row<T>(u);
+                    if (i < R) belem(B, D, tr, r0 + i, j0 + tx) = (double)acc[u];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (m < 0) return;
+    // column side (diagonal block only): columns r0.. for every row
+    for (int i0 = 0; i0 < m; i0 += RC) {
+        const int ni = min(RC, m - i0);
+        for (int e = threadIdx.x; e < R * RC; e += NT) {
+            int i = e / R, k = e % R;
+            slab[k * RC + i] = i < ni ? (T)B[(size_t)(i0 + i) * D + r0 + k] : (T)0;
+        }
+        __syncthreads();
+        for (int jb = 0; jb < R; jb += 8 * NU) {
+            rot_product<T, NU>(slab, vs, V, D, R, jb, acc);
+            if (tx < ni) {
+#pragma unroll
+                for (int u = 0; u < NU; ++u) {
+                    int j = jb + rot_row<T>(u);
+                    if (j < R) B[(size_t)(i0 + tx) * D + r0 + j] = (double)acc[u];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// row groups of k_rotate (8 * NU rows per pass) for blocks of dimension D
+__host__ __device__ constexpr int rotate_nu(int D) { return D <= 64 ? 8 : D <= 128 ? 16 : 32; }
+
+// shared memory of k_rotate for blocks of dimension at most D
+template <typename T>
+__host__ __device__ constexpr size_t rotate_smem(int D) {
+    return ((size_t)D * RC + (size_t)RK * 8 * rotate_nu(D)) * sizeof(T);
+}
+
+// NU = rotate_nu(D) of the level (R <= D; rows beyond 8 * NU take more passes)
+template <typename T, int NU>
 __global__ void __launch_bounds__(NT) k_rotate(FactorArgs A) {
+    HbScope hb_(2);
+    const int ci = blockIdx.x / A.nrow_max, b = blockIdx.x % A.nrow_max, lane = blockIdx.y;
+    if (lane >= *A.active || b >= A.nrow[ci]) return;
+    extern __shared__ __align__(16) unsigned char rot_smem[];
+    const int D = A.D, LN = A.lanes;
+    const int p = A.cl[ci];
+    const double* scr = A.scratch + ((size_t)ci * LN + lane) * A.lay.total;
+    const int* hdr = (const int*)(scr + A.lay.hdr);
+    if (!hdr[4]) return;
+    const int r0 = hdr[2], t = hdr[3];
+    const int m = A.dim[p * LN + lane];
+    const int R = m - r0;
+    const double* Vq = scr + A.lay.vq;
+    const int x = A.rowblk_other[ci * A.nrow_max + b];
+    const int tr = A.rowblk_trans[ci * A.nrow_max + b];
+    double* B = slot_ptr(A.slots, A.rowblk[ci * A.nrow_max + b], LN, lane, D);
+    {
+        const int dxl = live_rows(A, x, lane), dqa = A.dim[x * LN + lane];
+        if (m < 0 || m > D || r0 < 0 || r0 > m || t < 0 || t > R || dxl < 0 || dxl > D || dqa < 0 || dqa > D) {
+            if (threadIdx.x == 0) report_bad(A.err, 2, m, r0, t, dqa);
+            return;
+        }
+    }
+    double fl = 0.0;
+    if (t > 0) {
+        // rows r0.. of p: new = Vq^T old over the live columns of x; for the
+        // diagonal block also columns r0..: new = old Vq
+        const int dx = (x == p) ? m : live_rows(A, x, lane);
+        T* slab = reinterpret_cast<T*>(rot_smem);
+        T* vs = slab + (size_t)D * RC;
+        const int mcol = (x == p) ? m : -1;
+        rotate_block<T, NU>(B, D, tr, r0, R, dx, mcol, Vq, slab, vs);
+        fl += 2.0 * R * (double)R * dx;
+        if (x == p) fl += 2.0 * m * (double)R * R;
+    }
+    if (A.rowblk_fill[ci * A.nrow_max + b]) {   // drop the remaining redundant rows
+        const int dq = A.dim[x * LN + lane];
+        const int rows = m - (r0 + t);
+        for (int e = threadIdx.x; e < rows * dq; e += NT) {
+            int i = e / dq, j = e % dq;
+            belem(B, D, tr, r0 + t + i, j) = 0.0;
+        }
+    }
+    if (threadIdx.x == 0 && fl > 0.0) add_stats(A.stats, H2_KIND_ROTATE, fl, 8.0 * fl / R);
+}
+
+// FP64 path: one output per thread and step over the exact R x nj outputs of
+// each pass (no padded rows or columns: every DFMA is algorithmic)
+__global__ void __launch_bounds__(NT) k_rotate_fp64(FactorArgs A) {
     HbScope hb_(2);
     const int ci = blockIdx.x / A.nrow_max, b = blockIdx.x % A.nrow_max, lane = blockIdx.y;
     if (lane >= *A.active || b >= A.nrow[ci]) return;
@@ -286,9 +649,9 @@ __global__ void __launch_bounds__(NT) k_rotate(FactorArgs A) {
             __syncthreads();
             for (int e = threadIdx.x; e < R * nj; e += NT) {
                 int i = e / nj, j = e % nj;
-                T v = 0;
-                for (int k = 0; k < R; ++k) v += (T)Vq[(size_t)k * D + i] * (T)tile[k * RC + j];
-                belem(B, D, tr, r0 + i, j0 + j) = (double)v;
+                double v = 0.0;
+                for (int k = 0; k < R; ++k) v += Vq[(size_t)k * D + i] * tile[k * RC + j];
+                belem(B, D, tr, r0 + i, j0 + j) = v;
             }
             __syncthreads();
         }
@@ -303,9 +666,9 @@ __global__ void __launch_bounds__(NT) k_rotate(FactorArgs A) {
                 __syncthreads();
                 for (int e = threadIdx.x; e < ni * R; e += NT) {
                     int i = e / R, j = e % R;
-                    T v = 0;
-                    for (int k = 0; k < R; ++k) v += (T)tile[k * RC + i] * (T)Vq[(size_t)k * D + j];
-                    B[(size_t)(i0 + i) * D + r0 + j] = (double)v;
+                    double v = 0.0;
+                    for (int k = 0; k < R; ++k) v += tile[k * RC + i] * Vq[(size_t)k * D + j];
+                    B[(size_t)(i0 + i) * D + r0 + j] = v;
                 }
                 __syncthreads();
             }
@@ -390,6 +753,10 @@ __global__ void __launch_bounds__(NTH) k_ldl(FactorArgs A, int use_smem) {
 // (JB columns per block: a parallel update from the solved columns, then a
 // short per-row solve inside the block)
 constexpr int JB = 8;
+// T is the arithmetic of the solve and the type W and Y are stored in: double
+// (FP64 path) or float (mixed path: the FP64 factor L, D of the LDL step is
+// rounded to FP32, as are the products that form the Schur update)
+template <typename T>
 __global__ void __launch_bounds__(NT) k_trsm(FactorArgs A, int use_smem) {
     HbScope hb_(4);
     const int ci = blockIdx.x / A.ntarg_max, ti = blockIdx.x % A.ntarg_max, lane = blockIdx.y;
@@ -424,36 +791,37 @@ __global__ void __launch_bounds__(NT) k_trsm(FactorArgs A, int use_smem) {
                   8.0 * 3.0 * rows * (double)Rp);
     }
     if (rows <= 0) return;
-    // L, D and the pivots: staged in shared memory when they fit
+    // L, D and the pivots: staged in shared memory (as T) when they fit
     const double* F = scr + A.lay.f;
     const int* perm = (const int*)(scr + A.lay.iperm);
     const int* piv = perm + D;
-    const double* sL = F;
-    int ldl = D;
+    const T* sL = nullptr;
     const int* sperm = perm;
     const int* spiv = piv;
     if (use_smem) {
-        double* L2 = sh;                               // Rp x Rp
-        int* p2 = (int*)(sh + (size_t)Rp * Rp);
+        T* L2 = reinterpret_cast<T*>(sh);                        // Rp x Rp
+        int* p2 = reinterpret_cast<int*>(L2 + (size_t)Rp * Rp);
         int* v2 = p2 + Rp;
-        for (int e = threadIdx.x; e < Rp * Rp; e += NT) L2[e] = F[(size_t)(e / Rp) * D + e % Rp];
+        for (int e = threadIdx.x; e < Rp * Rp; e += NT) L2[e] = (T)F[(size_t)(e / Rp) * D + e % Rp];
         for (int e = threadIdx.x; e < Rp; e += NT) { p2[e] = perm[e]; v2[e] = piv[e]; }
         sL = L2;
-        ldl = Rp;
         sperm = p2;
         spiv = v2;
     }
     __syncthreads();
-    auto Lx = [&](int j, int k) {   // L(j, k), k < j, of the unit lower factor
-        return (spiv[k] == 2 && j == k + 1) ? 0.0 : sL[(size_t)j * ldl + k];
+    auto Fx = [&](int j, int k) -> T {  // entry (j, k) of the packed factor
+        return use_smem ? sL[(size_t)j * Rp + k] : (T)F[(size_t)j * D + k];
+    };
+    auto Lx = [&](int j, int k) -> T {  // L(j, k), k < j, of the unit lower factor
+        return (spiv[k] == 2 && j == k + 1) ? (T)0 : Fx(j, k);
     };
     const int tr = A.targ_trans[ci * A.ntarg_max + ti];
     const double* B = slot_ptr(A.slots, A.targ_slot[ci * A.ntarg_max + ti], LN, lane, D);
-    double* W = scr + A.lay.w + (size_t)ti * D * D;
-    double* Y = scr + A.lay.y + (size_t)ti * D * D;
+    T* W = reinterpret_cast<T*>(scr + A.lay.w + (size_t)ti * D * D);
+    T* Y = reinterpret_cast<T*>(scr + A.lay.y + (size_t)ti * D * D);
     for (int e = threadIdx.x; e < rows * Rp; e += NT) {       // W = S_ap^{.R} P
         int i = e / Rp, j = e % Rp;
-        W[(size_t)i * D + j] = tr ? B[(size_t)(rk1 + sperm[j]) * D + i] : B[(size_t)i * D + rk1 + sperm[j]];
+        W[(size_t)i * D + j] = (T)(tr ? B[(size_t)(rk1 + sperm[j]) * D + i] : B[(size_t)i * D + rk1 + sperm[j]]);
     }
     __syncthreads();
     for (int jb = 0; jb < Rp; jb += JB) {
@@ -461,17 +829,17 @@ __global__ void __launch_bounds__(NT) k_trsm(FactorArgs A, int use_smem) {
         if (jb > 0) {
             for (int e = threadIdx.x; e < rows * nb; e += NT) {
                 int i = e / nb, j = jb + e % nb;
-                double v = W[(size_t)i * D + j];
-                const double* wi = W + (size_t)i * D;
+                T v = W[(size_t)i * D + j];
+                const T* wi = W + (size_t)i * D;
                 for (int k = 0; k < jb; ++k) v -= wi[k] * Lx(j, k);
                 W[(size_t)i * D + j] = v;
             }
             __syncthreads();
         }
         for (int i = threadIdx.x; i < rows; i += NT) {
-            double* wi = W + (size_t)i * D;
+            T* wi = W + (size_t)i * D;
             for (int j = jb + 1; j < jb + nb; ++j) {
-                double v = wi[j];
+                T v = wi[j];
                 for (int k = jb; k < j; ++k) v -= wi[k] * Lx(j, k);
                 wi[j] = v;
             }
@@ -480,16 +848,15 @@ __global__ void __launch_bounds__(NT) k_trsm(FactorArgs A, int use_smem) {
     }
     for (int e = threadIdx.x; e < rows * Rp; e += NT) {       // Y = W D^{-1}
         int i = e / Rp, j = e % Rp;
-        const double* wi = W + (size_t)i * D;
-        double v;
+        const T* wi = W + (size_t)i * D;
+        T v;
         if (spiv[j] == 1) {
-            v = wi[j] * (1.0 / sL[(size_t)j * ldl + j]);
+            v = wi[j] * ((T)1 / Fx(j, j));
         } else {
             int j0 = spiv[j] == 2 ? j : j - 1;
-            double a0 = sL[(size_t)j0 * ldl + j0], b0 = sL[(size_t)(j0 + 1) * ldl + j0],
-                   c0 = sL[(size_t)(j0 + 1) * ldl + j0 + 1];
-            double idet = 1.0 / (a0 * c0 - b0 * b0);
-            double w0 = wi[j0], w1 = wi[j0 + 1];
+            T a0 = Fx(j0, j0), b0 = Fx(j0 + 1, j0), c0 = Fx(j0 + 1, j0 + 1);
+            T idet = (T)1 / (a0 * c0 - b0 * b0);
+            T w0 = wi[j0], w1 = wi[j0 + 1];
             v = (j == j0) ? (w0 * c0 - w1 * b0) * idet : (w1 * a0 - w0 * b0) * idet;
         }
         Y[(size_t)i * D + j] = v;
@@ -508,8 +875,9 @@ struct SchurArgs {
 };
 
 // S_ab[i0:i0+32, j0:j0+32] -= W_a Y_b^T (Eq. blr2-diag-schur).  T is the
-// arithmetic of the products: double (FP64 path) or float (mixed path: FP32
-// products and accumulation, the FP64 block updated by the rounded result).
+// arithmetic of the products and the type k_trsm stored W, Y in: double (FP64
+// path) or float (mixed path: FP32 products and accumulation, the FP64 block
+// updated by the rounded result).
 template <typename T>
 __global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
     HbScope hb_(5);
@@ -529,8 +897,8 @@ __global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
     }
     const int i0 = (tile / A.tdim) * TS, j0 = (tile % A.tdim) * TS;
     if (i0 >= ra || j0 >= rb) return;
-    const double* W = scr + A.lay.w + (size_t)P.ta * D * D;
-    const double* Y = scr + A.lay.y + (size_t)P.tb * D * D;
+    const T* W = reinterpret_cast<const T*>(scr + A.lay.w + (size_t)P.ta * D * D);
+    const T* Y = reinterpret_cast<const T*>(scr + A.lay.y + (size_t)P.tb * D * D);
     __shared__ T sW[TS][TS + 1], sY[TS][TS + 1];
     const int tx = threadIdx.x % TS, ty = threadIdx.x / TS;   // ty in 0..7
     T acc[4] = {0, 0, 0, 0};
@@ -538,8 +906,8 @@ __global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
         const int kc = min(TS, Rp - k0);
         for (int e = threadIdx.x; e < TS * TS; e += NT) {
             int r = e / TS, k = e % TS;
-            sW[r][k] = (i0 + r < ra && k < kc) ? (T)W[(size_t)(i0 + r) * D + k0 + k] : (T)0;
-            sY[r][k] = (j0 + r < rb && k < kc) ? (T)Y[(size_t)(j0 + r) * D + k0 + k] : (T)0;
+            sW[r][k] = (i0 + r < ra && k < kc) ? W[(size_t)(i0 + r) * D + k0 + k] : (T)0;
+            sY[r][k] = (j0 + r < rb && k < kc) ? Y[(size_t)(j0 + r) * D + k0 + k] : (T)0;
         }
         __syncthreads();
 #pragma unroll 8
@@ -556,6 +924,71 @@ __global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
         int i = i0 + ty + 8 * u, j = j0 + tx;
         if (i < ra && j < rb) belem(B, D, P.trans, i, j) -= (double)acc[u];
     }
+}
+
+// Mixed path: S_ab[i0:i0+64, j0:j0+64] -= W_a Y_b^T (Eq. blr2-diag-schur) with
+// FP32 products and accumulation; W, Y were stored in FP32 by k_trsm<float>.
+// Thread (tx, ty) owns rows ty + 16 i and columns tx + 16 j (i, j < 4): the W
+// reads are warp broadcasts, the Y reads hit 16 distinct banks, and the FP64
+// read-modify-write of S is coalesced along rows.
+constexpr int TSF = 64;
+__global__ void __launch_bounds__(NT) k_schur_f32(SchurArgs A) {
+    HbScope hb_(5);
+    const int lane = blockIdx.y;
+    if (lane >= *A.active) return;
+    const int pi = blockIdx.x / A.tiles_per_pair, tile = blockIdx.x % A.tiles_per_pair;
+    const SchurPair P = A.pairs[pi];
+    const int D = A.D;
+    const double* scr = A.scratch + ((size_t)P.elim * A.lanes + lane) * A.lay.total;
+    const int* hdr = (const int*)(scr + A.lay.hdr);
+    const int Rp = hdr[1];
+    if (Rp <= 0) return;
+    const int ra = hdr[HDR_ROWS + P.ta], rb = hdr[HDR_ROWS + P.tb];
+    if (Rp > D || ra < 0 || ra > D || rb < 0 || rb > D) {
+        if (threadIdx.x == 0 && tile == 0) report_bad(A.err, 5, Rp, ra, rb, D);
+        return;
+    }
+    const int i0 = (tile / A.tdim) * TSF, j0 = (tile % A.tdim) * TSF;
+    if (i0 >= ra || j0 >= rb) return;
+    const float* W = reinterpret_cast<const float*>(scr + A.lay.w + (size_t)P.ta * D * D);
+    const float* Y = reinterpret_cast<const float*>(scr + A.lay.y + (size_t)P.tb * D * D);
+    __shared__ float sW[TSF][33], sY[TSF][33];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < Rp; k0 += 32) {
+        const int kc = min(32, Rp - k0);
+        for (int e = threadIdx.x; e < TSF * 32; e += NT) {
+            int r = e / 32, k = e % 32;
+            sW[r][k] = (i0 + r < ra && k < kc) ? W[(size_t)(i0 + r) * D + k0 + k] : 0.f;
+            sY[r][k] = (j0 + r < rb && k < kc) ? Y[(size_t)(j0 + r) * D + k0 + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < kc; ++k) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = sW[ty + 16 * i][k];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = sY[tx + 16 * j][k];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+    double* B = slot_ptr(A.slots, P.slot, A.lanes, lane, D);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int r = i0 + ty + 16 * i, c = j0 + tx + 16 * j;
+            if (r < ra && c < rb) belem(B, D, P.trans, r, c) -= (double)acc[i][j];
+        }
 }
 
 // leaf level: copy Q^T A Q near blocks, subtract sigma on the diagonal, fill
@@ -772,6 +1205,9 @@ __global__ void k_finish(const unsigned long long* neg, const unsigned long long
 
 // ------------------------------------------------------------ workspace --
 constexpr size_t kSmemCap = 200 * 1024;   // dynamic shared memory staged per CTA at most
+constexpr size_t kSmemMax = 227 * 1024;   // opt-in limit per CTA
+// default Z width from which the recompression is shared by a cluster of QG CTAs
+constexpr size_t kWideFill = 4096;
 
 struct ColourDev {
     int ncl, ntarg_max, nrow_max, nfill_max, npairs, has_fill;
@@ -806,6 +1242,15 @@ static FactorState* state_of(h2_matrix* h) {
 }
 
 static int ensure_graph(h2_matrix* h, int mixed);
+// graphs unless the handle asks for plain launches or the environment
+// variable H2_NO_GRAPH=1 (a diagnostic) turns them off for the process
+static bool use_graphs(const h2_matrix* h) {
+    static const int no_graph = [] {
+        const char* e = getenv("H2_NO_GRAPH");
+        return e && e[0] == '1';
+    }();
+    return !no_graph && h->opt.graphs != 0;
+}
 int heartbeat_setup();
 
 int alloc_workspace(h2_matrix* h, int lanes) {
@@ -828,6 +1273,10 @@ int alloc_workspace(h2_matrix* h, int lanes) {
             const LevelDev& C = h->lev[l + 1];
             int skc = std::max(C.rbmax, std::min(fill_cap, C.dmax));
             D.dmax = std::max(1, 2 * skc);
+        }
+        if (rotate_smem<float>(D.dmax) > kSmemMax || (size_t)D.dmax * RC * sizeof(double) > kSmemMax) {
+            set_error("block dimension " + std::to_string(D.dmax) + " exceeds the shared-memory staging of the rotation kernel");
+            return H2_ERR_INVALID_ARG;
         }
     }
     size_t scratch_max = 0, merge_max = 0;
@@ -917,11 +1366,14 @@ int alloc_workspace(h2_matrix* h, int lanes) {
         }
         if ((rc = upload(&W.d_slot_of, D.slot_of)) || (rc = upload(&W.d_far_of, D.far_of))) return rc;
     }
-    CK(cudaFuncSetAttribute(k_rotate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
-    CK(cudaFuncSetAttribute(k_rotate<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_rotate_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_rotate<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_rotate<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_rotate<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     CK(cudaFuncSetAttribute(k_ldl<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
     CK(cudaFuncSetAttribute(k_ldl<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
-    CK(cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
     // buffers
     ws.d_slots.assign(L + 1, nullptr);
     ws.d_dim.assign(L + 1, nullptr);
@@ -948,8 +1400,10 @@ int alloc_workspace(h2_matrix* h, int lanes) {
     // capture the batch graphs now, while nothing else runs on the device:
     // a capture never overlaps other handles' work on other streams
     CK(cudaStreamSynchronize(h->stream));
-    if ((rc = ensure_graph(h, 0))) return rc;
-    if (h->opt.precision == H2_PREC_MIXED && (rc = ensure_graph(h, 1))) return rc;
+    if (use_graphs(h)) {
+        if ((rc = ensure_graph(h, 0))) return rc;
+        if (h->opt.precision == H2_PREC_MIXED && (rc = ensure_graph(h, 1))) return rc;
+    }
     CK(cudaStreamSynchronize(h->stream));
     return H2_OK;
 }
@@ -1011,13 +1465,23 @@ static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, 
             const int Dm = D.dmax;
             if (C.has_fill) {
                 B(H2_KIND_RECOMP);
-                k_recomp<<<dim3(C.ncl, LN), NT, 0, st>>>(fa);
+                const int wide = h->opt.recomp_cluster_cols;
+                if (wide >= 0 && (size_t)C.nfill_max * Dm >= (wide > 0 ? (size_t)wide : kWideFill))
+                    k_recomp_cluster<<<dim3(C.ncl * QG, LN), NT, (size_t)Dm * sizeof(double), st>>>(fa);
+                else
+                    k_recomp<<<dim3(C.ncl, LN), NT, 0, st>>>(fa);
                 E();
                 B(H2_KIND_ROTATE);
-                if (mixed)
-                    k_rotate<float><<<dim3(C.ncl * C.nrow_max, LN), NT, (size_t)Dm * RC * sizeof(double), st>>>(fa);
+                const dim3 grid(C.ncl * C.nrow_max, LN);
+                const size_t sm = rotate_smem<float>(Dm);
+                if (!mixed)
+                    k_rotate_fp64<<<grid, NT, (size_t)Dm * RC * sizeof(double), st>>>(fa);
+                else if (rotate_nu(Dm) == 8)
+                    k_rotate<float, 8><<<grid, NT, sm, st>>>(fa);
+                else if (rotate_nu(Dm) == 16)
+                    k_rotate<float, 16><<<grid, NT, sm, st>>>(fa);
                 else
-                    k_rotate<double><<<dim3(C.ncl * C.nrow_max, LN), NT, (size_t)Dm * RC * sizeof(double), st>>>(fa);
+                    k_rotate<float, 32><<<grid, NT, sm, st>>>(fa);
                 E();
             }
             const size_t sm_ldl = ((size_t)Dm * Dm + 4 * (size_t)Dm) * sizeof(double);
@@ -1031,14 +1495,17 @@ static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, 
             const size_t sm_trsm = (size_t)Dm * Dm * sizeof(double) + 2 * (size_t)Dm * sizeof(int);
             const int trsm_smem = sm_trsm <= kSmemCap ? 1 : 0;
             B(H2_KIND_TRSM);
-            k_trsm<<<dim3(C.ncl * C.ntarg_max, LN), NT, trsm_smem ? sm_trsm : 0, st>>>(fa, trsm_smem);
+            if (mixed)
+                k_trsm<float><<<dim3(C.ncl * C.ntarg_max, LN), NT, trsm_smem ? sm_trsm : 0, st>>>(fa, trsm_smem);
+            else
+                k_trsm<double><<<dim3(C.ncl * C.ntarg_max, LN), NT, trsm_smem ? sm_trsm : 0, st>>>(fa, trsm_smem);
             E();
-            int tdim = (D.dmax + TS - 1) / TS;
+            const int tdim = (D.dmax + (mixed ? TSF : TS) - 1) / (mixed ? TSF : TS);
             SchurArgs sa{ws.d_slots[l], D.dmax, LN, C.pairs, tdim * tdim, tdim, ws.d_scratch, W.lay,
                          fs->d_active, ws.d_err};
             B(H2_KIND_SCHUR);
             if (mixed)
-                k_schur<float><<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
+                k_schur_f32<<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
             else
                 k_schur<double><<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
             E();
@@ -1079,16 +1546,11 @@ static int ensure_graph(h2_matrix* h, int mixed) {
     return H2_OK;
 }
 
-// launch one batch of the lanes already in ws.d_shifts (count set on device);
-// the environment variable H2_NO_GRAPH=1 (a diagnostic) launches the same
-// kernels one by one instead of replaying the captured graph
+// launch one batch of the lanes already in ws.d_shifts (count set on device):
+// replay the captured graph, or launch the same kernels one by one
 static int launch_batch(h2_matrix* h, int mixed) {
-    static const int no_graph = [] {
-        const char* e = getenv("H2_NO_GRAPH");
-        return e && e[0] == '1';
-    }();
-    if (no_graph) {
-        enqueue_factorization(h, h->stream, nullptr, mixed);
+    if (!use_graphs(h)) {
+        h->kernels_per_batch = enqueue_factorization(h, h->stream, nullptr, mixed);
         CK(cudaGetLastError());
         return H2_OK;
     }
@@ -1107,7 +1569,7 @@ int run_inertia(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts,
         set_error("h2_inertia_device: ns exceeds max_lanes");
         return H2_ERR_INVALID_ARG;
     }
-    int rc = ensure_graph(h, h->opt.precision == H2_PREC_MIXED);
+    int rc = use_graphs(h) ? ensure_graph(h, h->opt.precision == H2_PREC_MIXED) : H2_OK;
     if (rc) return rc;
     CK(cudaMemcpyAsync(ws.d_shifts, d_shifts, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
     k_set_int<<<1, 1, 0, st>>>(fs->d_active, ns);
