@@ -67,8 +67,9 @@ FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 (profiling recipe table); not i
 # profiles/k_schur_laplace2d_n1024_256lanes.md; valid for that workload and lane
 # count while the kernel's source is unchanged (sha256 prefix of its text)
 NCU_TRAFFIC = {"kernel": "k_schur", "workload": "laplace2d_n1024", "lanes": 256,
-               "bytes_per_launch": 327.2e6, "source_sha": "5a1bc59e734badc5"}
-KERNEL_REGIONS = {"k_schur": ("h2_factor.cu", "struct SchurArgs {", "// leaf level: copy")}
+               "bytes_per_launch": None, "source_sha": None}
+KERNEL_REGIONS = {"k_schur": ("h2_factor.cu", "struct SchurArgs {",
+                               "// FP64-accurate Schur products on the tensor cores")}
 
 
 def _peaks():
@@ -436,6 +437,44 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
                  "mixed_rounds": infm["last_mixed_rounds"], "bracket_resets": infm["bracket_resets"],
                  "lambda": float(outm[0]), "abs_diff_vs_fp64": float(abs(outm[0] - lam[0]))}
     Mx.close()
+    # ---- FP64 with the Schur-update products on the tensor cores (exact
+    # BF16 products of 7-bit digits, integer accumulation, one FP64 rounding)
+    Mt = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
+                      eta=WORKLOAD["eta"], max_lanes=lanes, stream=stream.cuda_stream,
+                      precision=pkg.H2_PREC_FP64_TC)
+    for i in range(args.warmup):
+        Mt.h2_inertia_device(d_sh[i], lanes, d_cnt[i], d_mp[i])
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(args.warmup, total):
+        Mt.h2_inertia_device(d_sh[i], lanes, d_cnt[i], d_mp[i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_tc = _max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    tc_same = bool(torch.equal(d_cnt, cnt_fp64))
+    ptc = Mt.h2_profile_batch(d_sh[args.warmup], lanes, d_cnt[args.warmup])
+    Mt.close()
+    Mte = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
+                       eta=WORKLOAD["eta"], max_lanes=args.eig_lanes, stream=stream.cuda_stream,
+                       precision=pkg.H2_PREC_FP64_TC)
+    latt = []
+    for i in range(args.eig_solves + 2):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        outt, ebt = Mte.h2_kth_eig([WORKLOAD["k"]], WORKLOAD["tol"])
+        latt.append(time.perf_counter() - t)
+    latt = np.array(latt[2:])
+    Mte.close()
+    tot_tc = sum(v["ms"] for v in ptc.values())
+    fp64_tc = {"mode": "FP64; Schur-update products on the tensor cores (8 exact 7-bit digits per entry, "
+                       "BF16 digit products summed exactly, one FP64 rounding per entry)",
+               "value": world * args.steps * lanes / (ms_tc / 1e3), "unit": "shifts/s",
+               "counts_equal_to_fp64": tc_same,
+               "eigs_per_s": float(1.0 / np.mean(latt)), "p50_ms": float(np.percentile(latt, 50) * 1e3),
+               "p99_ms": float(np.percentile(latt, 99) * 1e3), "lambda": float(outt[0]),
+               "abs_diff_vs_fp64": float(abs(outt[0] - lam[0])),
+               "schur_ms_per_launch": ptc["schur"]["ms"] / max(1, ptc["schur"]["launches"]),
+               "kernel_shares": {k: v["ms"] / tot_tc for k, v in ptc.items()}}
     # ---- the plain FP64 path: one shift per launch sequence (1 lane), kernels
     # launched one by one (no graph, no batching)
     Mp = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
@@ -477,7 +516,7 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
                      "rounds": info2["last_rounds"], "shifts_per_solve": info2["last_shifts"],
                      "lambda": lam[0], "err_bound": lam[1]},
             "build_s": build_s, "roofline": roof, "clocks": clocks, "precision": precision,
-            "plain_fp64": plain, "serving": serving_res}
+            "fp64_tc": fp64_tc, "plain_fp64": plain, "serving": serving_res}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         sample = list(sh[args.warmup][:: max(1, lanes // (2 * cores))][:2 * cores])

@@ -63,13 +63,21 @@ typedef struct {
 #define H2_ADM_CENTER 1  /* (diam c + diam d)/2 <= eta * |center c - center d| */
 
 #define H2_PREC_FP64  0  /* every step in FP64 */
-#define H2_PREC_MIXED 1  /* Schur-update and rotation products in FP32 (FP32
-                            accumulation); storage, Bunch-Kaufman pivoting,
-                            pivot counts and interval updates in FP64; guarded
-                            shifts re-run in FP64 (see h2_inertia, h2_kth_eig) */
+#define H2_PREC_MIXED 1  /* Schur-update, triangular-solve and rotation
+                            products in FP32 (FP32 accumulation); storage,
+                            Bunch-Kaufman pivoting, pivot counts and interval
+                            updates in FP64; guarded shifts re-run in FP64
+                            (see h2_inertia, h2_kth_eig) */
+#define H2_PREC_FP64_TC 2 /* as H2_PREC_FP64, but the Schur-update products
+                            W_a Y_b^T run on the tensor cores: 8 exact 7-bit
+                            integer digits per FP64 entry (row-scaled), BF16
+                            digit products summed exactly, one FP64 rounding
+                            per entry; the error stays below 2^-53 of the
+                            result plus 2^-56 K of the row-scale products */
 
 typedef struct {
-    int precision;       /* H2_PREC_FP64 (default) or H2_PREC_MIXED */
+    int precision;       /* H2_PREC_FP64 (default), H2_PREC_MIXED or
+                            H2_PREC_FP64_TC */
     int admissibility;   /* H2_ADM_BOX (default) or H2_ADM_CENTER */
     double eps_h2;       /* truncation tolerance relative to ||A||_inf (Sec. 3.1,
                             eps_H2; default 1e-10 = 1e-2 * 1e-8, Sec. 5) */

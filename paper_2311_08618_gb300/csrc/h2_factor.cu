@@ -926,6 +926,176 @@ __global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
     }
 }
 
+// FP64-accurate Schur products on the tensor cores (precision H2_PREC_FP64_TC).
+// Every row of W (and of Y) is scaled by 2^e with |x| < 2^e over the row and
+// cut into OZP = 8 signed 7-bit integer digits taken from the 53-bit
+// significand: x = sign * 2^e * sum_p d_p 2^(-7p), d_p in [0, 127], exact up to
+// the truncated bits below 2^(e-56).  Digits are exact in BF16, so
+//   sum_k W_ik Y_jk = 2^(e_i + f_j) sum_t 2^(-7t) L_t,
+//   L_t = sum_{p+q=t} sum_k d_p(W_ik) d_q(Y_jk),
+// and the terms with t = p + q > 9 (below 2^-70 of the row scales) are dropped:
+// 36 of the 64 digit pairs remain.  Over a chunk of OZK = 32 values of k,
+// |L_t| <= 8 * 32 * 127^2 < 2^22, and every partial sum an MMA forms is an
+// integer below 2^24: BF16 products with FP32 accumulation (mma.sync
+// m16n8k16) are exact.  Per chunk the level sums are folded into two exact
+// int64 accumulators, hi = sum_{t=2..5} L_t 2^(7(5-t)) and lo = sum_{t=6..9}
+// L_t 2^(7(9-t)); the product is rounded to FP64 once, from
+// hi 2^-35 + lo 2^-63.  (Splitting FP64 operands into small-integer slices
+// whose products a low-precision unit sums exactly is the scheme of Ozaki,
+// Ogita, Oishi and Rump, 2012.)
+constexpr int OZP = 8;
+constexpr int OZK = 32;
+constexpr int OZLD = OZK + 8;   // BF16 row stride: fragment loads hit 32 distinct banks
+
+// biased exponent field of x (0 for zero and subnormals)
+__device__ __forceinline__ int oz_expo(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+// the 8 BF16 digits of x for a row whose largest biased exponent is emax
+__device__ __forceinline__ void oz_digits(double x, int emax, uint32_t (&d)[OZP]) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    unsigned long long F = 0;
+    if (ex != 0) {
+        const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
+        const int sh = ex - emax + 3;            // F = |x| 2^(56 - e) = M 2^sh < 2^56
+        F = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> -sh) : 0ull);
+    }
+    const uint32_t sg = (uint32_t)(b >> 48) & 0x8000u;
+#pragma unroll
+    for (int p = 0; p < OZP; ++p) {
+        const uint32_t v = (uint32_t)(F >> (49 - 7 * p)) & 127u;
+        const float f = __uint_as_float(0x4B000000u | v) - 8388608.0f;   // (float)v, exact
+        d[p] = (__float_as_uint(f) >> 16) | (v ? sg : 0u);              // BF16 bits, exact
+    }
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// an integer-valued float below 2^22 in magnitude, as int (exact)
+__device__ __forceinline__ long long oz_int(float v) {
+    return (long long)(__float_as_int(v + 12582912.0f) - 0x4B400000);
+}
+
+__global__ void __launch_bounds__(NT) k_schur_oz(SchurArgs A) {
+    HbScope hb_(5);
+    const int lane = blockIdx.y;
+    if (lane >= *A.active) return;
+    const int pi = blockIdx.x / A.tiles_per_pair, tile = blockIdx.x % A.tiles_per_pair;
+    const SchurPair P = A.pairs[pi];
+    const int D = A.D;
+    const double* scr = A.scratch + ((size_t)P.elim * A.lanes + lane) * A.lay.total;
+    const int* hdr = (const int*)(scr + A.lay.hdr);
+    const int Rp = hdr[1];
+    if (Rp <= 0) return;
+    const int ra = hdr[HDR_ROWS + P.ta], rb = hdr[HDR_ROWS + P.tb];
+    if (Rp > D || ra < 0 || ra > D || rb < 0 || rb > D) {
+        if (threadIdx.x == 0 && tile == 0) report_bad(A.err, 5, Rp, ra, rb, D);
+        return;
+    }
+    const int i0 = (tile / A.tdim) * TS, j0 = (tile % A.tdim) * TS;
+    if (i0 >= ra || j0 >= rb) return;
+    const double* W = scr + A.lay.w + (size_t)P.ta * D * D + (size_t)i0 * D;
+    const double* Y = scr + A.lay.y + (size_t)P.tb * D * D + (size_t)j0 * D;
+    const int nr = min(TS, ra - i0), nc = min(TS, rb - j0);
+    __shared__ __align__(16) uint16_t sA[OZP][TS][OZLD], sB[OZP][TS][OZLD];
+    __shared__ int sEa[TS], sEb[TS];
+    const int w = threadIdx.x / 32, l = threadIdx.x % 32, gid = l / 4, tig = l % 4;
+    // row scales: the largest exponent of each row over all k
+    for (int r = w; r < TS; r += NT / 32) {
+        int ea = 0, eb = 0;
+        for (int k = l; k < Rp; k += 32) {
+            if (r < nr) ea = max(ea, oz_expo(W[(size_t)r * D + k]));
+            if (r < nc) eb = max(eb, oz_expo(Y[(size_t)r * D + k]));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, o));
+            eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, o));
+        }
+        if (l == 0) { sEa[r] = ea; sEb[r] = eb; }
+    }
+    __syncthreads();
+    // warp tile: rows 16 mi .. 16 mi + 15, columns 8 ni .. 8 ni + 7
+    const int mi = w / 4, ni = w % 4;
+    const bool act = 16 * mi < nr && 8 * ni < nc;      // warp-uniform
+    long long hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+    for (int k0 = 0; k0 < Rp; k0 += OZK) {
+        const int kc = min(OZK, Rp - k0);
+        // digits of this chunk: 2 operands x TS rows x OZK/2 pairs of k
+        for (int e = threadIdx.x; e < 2 * TS * (OZK / 2); e += NT) {
+            const int op = e / (TS * (OZK / 2)), rem = e % (TS * (OZK / 2));
+            const int r = rem / (OZK / 2), k = 2 * (rem % (OZK / 2));
+            const double* src = op ? Y : W;
+            const int nrow = op ? nc : nr, em = op ? sEb[r] : sEa[r];
+            const double x0 = (r < nrow && k < kc) ? src[(size_t)r * D + k0 + k] : 0.0;
+            const double x1 = (r < nrow && k + 1 < kc) ? src[(size_t)r * D + k0 + k + 1] : 0.0;
+            uint32_t d0[OZP], d1[OZP];
+            oz_digits(x0, em, d0);
+            oz_digits(x1, em, d1);
+            uint16_t (*dst)[TS][OZLD] = op ? sB : sA;
+#pragma unroll
+            for (int p = 0; p < OZP; ++p) *reinterpret_cast<uint32_t*>(&dst[p][r][k]) = d0[p] | (d1[p] << 16);
+        }
+        __syncthreads();
+        if (act) {
+            float acc[OZP][4];
+#pragma unroll
+            for (int t = 0; t < OZP; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+            for (int s0 = 0; s0 < kc; s0 += 16) {
+                uint32_t b[OZP][2];
+#pragma unroll
+                for (int q = 0; q < OZP; ++q) {
+                    b[q][0] = *reinterpret_cast<const uint32_t*>(&sB[q][8 * ni + gid][s0 + 2 * tig]);
+                    b[q][1] = *reinterpret_cast<const uint32_t*>(&sB[q][8 * ni + gid][s0 + 2 * tig + 8]);
+                }
+#pragma unroll
+                for (int p = 0; p < OZP; ++p) {
+                    uint32_t a[4];
+                    a[0] = *reinterpret_cast<const uint32_t*>(&sA[p][16 * mi + gid][s0 + 2 * tig]);
+                    a[1] = *reinterpret_cast<const uint32_t*>(&sA[p][16 * mi + gid + 8][s0 + 2 * tig]);
+                    a[2] = *reinterpret_cast<const uint32_t*>(&sA[p][16 * mi + gid][s0 + 2 * tig + 8]);
+                    a[3] = *reinterpret_cast<const uint32_t*>(&sA[p][16 * mi + gid + 8][s0 + 2 * tig + 8]);
+#pragma unroll
+                    for (int q = 0; q < OZP - p; ++q) mma_bf16(acc[p + q], a, b[q][0], b[q][1]);
+                }
+            }
+            // level t = p + q + 2: hi gets t = 2..5, lo gets t = 6..9 (exact)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                long long h = oz_int(acc[0][c]);
+                h = h * 128 + oz_int(acc[1][c]);
+                h = h * 128 + oz_int(acc[2][c]);
+                h = h * 128 + oz_int(acc[3][c]);
+                long long g = oz_int(acc[4][c]);
+                g = g * 128 + oz_int(acc[5][c]);
+                g = g * 128 + oz_int(acc[6][c]);
+                g = g * 128 + oz_int(acc[7][c]);
+                hi[c] += h;
+                lo[c] += g;
+            }
+        }
+        __syncthreads();
+    }
+    if (!act) return;
+    double* B = slot_ptr(A.slots, P.slot, A.lanes, lane, D);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int r = 16 * mi + gid + (c >= 2 ? 8 : 0), q = 8 * ni + 2 * tig + (c & 1);
+        if (r < nr && q < nc) {
+            const int e = (sEa[r] - 1022) + (sEb[q] - 1022);
+            const double v = fma((double)lo[c], 0x1p-28, (double)hi[c]);   // exact operands, one rounding
+            belem(B, D, P.trans, i0 + r, j0 + q) -= ldexp(v, e - 35);
+        }
+    }
+}
+
 // Mixed path: S_ab[i0:i0+64, j0:j0+64] -= W_a Y_b^T (Eq. blr2-diag-schur) with
 // FP32 products and accumulation; W, Y were stored in FP32 by k_trsm<float>.
 // Thread (tx, ty) owns rows ty + 16 i and columns tx + 16 j (i, j < 4): the W
@@ -1506,6 +1676,8 @@ static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, 
             B(H2_KIND_SCHUR);
             if (mixed)
                 k_schur_f32<<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
+            else if (h->opt.precision == H2_PREC_FP64_TC)
+                k_schur_oz<<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
             else
                 k_schur<double><<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
             E();
