@@ -85,23 +85,38 @@ struct HbScope {
 
 // scratch layout of one elimination (offsets in doubles)
 struct ScratchLayout {
-    size_t z, vr, vq, tmp, f, iperm, hdr, w, y, total;
+    size_t z, vr, vq, tmp, f, iperm, hdr, w, y;
+    // FP64_TC only (dk > 0): BF16 digit planes [target][digit][row][dk] of W
+    // and Y (k padded with zero digits to dk, a multiple of 32) and the
+    // largest biased exponent of every row [target][row]
+    size_t wd, yd, we, ye;
+    int dk;
+    size_t total;
 };
 
-static ScratchLayout scratch_layout(int D, int nfill_max, int ntarg_max) {
+static ScratchLayout scratch_layout(int D, int nfill_max, int ntarg_max, bool digits) {
     ScratchLayout s{};
     size_t zcols = (size_t)std::max(nfill_max, 1) * D;
     size_t o = 0;
-    s.z = o; o += (size_t)D * zcols;
-    s.vr = o; o += (size_t)D * D;
-    s.vq = o; o += (size_t)D * D;
-    s.tmp = o; o += (size_t)D * D;
-    s.f = o; o += (size_t)D * D;
-    s.iperm = o; o += (size_t)D;              // 2*D ints
-    s.hdr = o; o += 8 + (size_t)(ntarg_max + 1) / 2 + 1;   // ints
-    s.w = o; o += (size_t)ntarg_max * D * D;
-    s.y = o; o += (size_t)ntarg_max * D * D;
-    s.total = (o + 3) & ~(size_t)3;
+    auto al = [&]() { o = (o + 3) & ~(size_t)3; };   // 32-byte aligned regions
+    s.z = o; o += (size_t)D * zcols; al();
+    s.vr = o; o += (size_t)D * D; al();
+    s.vq = o; o += (size_t)D * D; al();
+    s.tmp = o; o += (size_t)D * D; al();
+    s.f = o; o += (size_t)D * D; al();
+    s.iperm = o; o += (size_t)D; al();              // 2*D ints
+    s.hdr = o; o += 8 + (size_t)(ntarg_max + 1) / 2 + 1; al();   // ints
+    s.w = o; o += (size_t)ntarg_max * D * D; al();
+    s.y = o; o += (size_t)ntarg_max * D * D; al();
+    if (digits) {
+        s.dk = (D + 31) / 32 * 32;
+        const size_t plane = (size_t)ntarg_max * 8 * D * s.dk / 4;    // halves -> doubles
+        s.wd = o; o += plane; al();
+        s.yd = o; o += plane; al();
+        s.we = o; o += ((size_t)ntarg_max * D + 1) / 2; al();
+        s.ye = o; o += ((size_t)ntarg_max * D + 1) / 2; al();
+    }
+    s.total = o;
     return s;
 }
 
@@ -748,6 +763,48 @@ __global__ void __launch_bounds__(NTH) k_ldl(FactorArgs A, int use_smem) {
     }
 }
 
+// Digits of the FP64_TC Schur products (see k_schur_oz).
+constexpr int OZP = 8;
+constexpr int OZK = 32;
+constexpr int OZLD = OZK + 8;   // BF16 row stride: fragment loads hit 32 distinct banks
+
+// biased exponent field of x (0 for zero and subnormals)
+__device__ __forceinline__ int oz_expo(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+// the 8 BF16 digits of x for a row whose largest biased exponent is emax
+__device__ __forceinline__ void oz_digits(double x, int emax, uint32_t (&d)[OZP]) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    unsigned long long F = 0;
+    if (ex != 0) {
+        const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
+        const int sh = ex - emax + 3;            // F = |x| 2^(56 - e) = M 2^sh < 2^56
+        F = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> -sh) : 0ull);
+    }
+    const uint32_t sg = (uint32_t)(b >> 48) & 0x8000u;
+#pragma unroll
+    for (int p = 0; p < OZP; ++p) {
+        const uint32_t v = (uint32_t)(F >> (49 - 7 * p)) & 127u;
+        const float f = __uint_as_float(0x4B000000u | v) - 8388608.0f;   // (float)v, exact
+        d[p] = (__float_as_uint(f) >> 16) | (v ? sg : 0u);              // BF16 bits, exact
+    }
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// an integer-valued float below 2^22 in magnitude, as int (exact)
+__device__ __forceinline__ long long oz_int(float v) {
+    return (long long)(__float_as_int(v + 12582912.0f) - 0x4B400000);
+}
+
 // ---- (iv) W_a = S_ap^{.R} P L^{-T}, Y_a = W_a D^{-1} (Eq. blr2-diag-elimination):
 // one CTA per (target, cluster, lane); column-blocked forward substitution
 // (JB columns per block: a parallel update from the solved columns, then a
@@ -861,6 +918,44 @@ __global__ void __launch_bounds__(NT) k_trsm(FactorArgs A, int use_smem) {
         }
         Y[(size_t)i * D + j] = v;
     }
+    if (A.lay.dk > 0) {          // FP64_TC: digit planes of W_a and Y_a, once
+        __syncthreads();
+        const int dk = A.lay.dk;
+        uint16_t* wd = reinterpret_cast<uint16_t*>(scr + A.lay.wd) + (size_t)ti * OZP * D * dk;
+        uint16_t* yd = reinterpret_cast<uint16_t*>(scr + A.lay.yd) + (size_t)ti * OZP * D * dk;
+        int* we = reinterpret_cast<int*>(scr + A.lay.we) + ti * D;
+        int* ye = reinterpret_cast<int*>(scr + A.lay.ye) + ti * D;
+        const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+        for (int r = w; r < rows; r += NT / 32) {
+            int ea = 0, eb = 0;
+            for (int k = l; k < Rp; k += 32) {
+                ea = max(ea, oz_expo((double)W[(size_t)r * D + k]));
+                eb = max(eb, oz_expo((double)Y[(size_t)r * D + k]));
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, o));
+                eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, o));
+            }
+            if (l == 0) { we[r] = ea; ye[r] = eb; }
+        }
+        __syncthreads();
+        const int npair = (Rp + 31) / 32 * 16;       // k pairs up to the padded width
+        for (int e = threadIdx.x; e < 2 * rows * npair; e += NT) {
+            const int op = e / (rows * npair), rem = e % (rows * npair);
+            const int r = rem / npair, k = 2 * (rem % npair);
+            const T* src = op ? Y : W;
+            const int em = op ? ye[r] : we[r];
+            const double x0 = k < Rp ? (double)src[(size_t)r * D + k] : 0.0;
+            const double x1 = k + 1 < Rp ? (double)src[(size_t)r * D + k + 1] : 0.0;
+            uint32_t d0[OZP], d1[OZP];
+            oz_digits(x0, em, d0);
+            oz_digits(x1, em, d1);
+            uint16_t* dst = op ? yd : wd;
+#pragma unroll
+            for (int p = 0; p < OZP; ++p)
+                *reinterpret_cast<uint32_t*>(&dst[((size_t)p * D + r) * dk + k]) = d0[p] | (d1[p] << 16);
+        }
+    }
 }
 
 struct SchurArgs {
@@ -943,48 +1038,7 @@ __global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
 // hi 2^-35 + lo 2^-63.  (Splitting FP64 operands into small-integer slices
 // whose products a low-precision unit sums exactly is the scheme of Ozaki,
 // Ogita, Oishi and Rump, 2012.)
-constexpr int OZP = 8;
-constexpr int OZK = 32;
-constexpr int OZLD = OZK + 8;   // BF16 row stride: fragment loads hit 32 distinct banks
-
-// biased exponent field of x (0 for zero and subnormals)
-__device__ __forceinline__ int oz_expo(double x) {
-    return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
-}
-
-// the 8 BF16 digits of x for a row whose largest biased exponent is emax
-__device__ __forceinline__ void oz_digits(double x, int emax, uint32_t (&d)[OZP]) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int ex = (int)((b >> 52) & 0x7ff);
-    unsigned long long F = 0;
-    if (ex != 0) {
-        const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
-        const int sh = ex - emax + 3;            // F = |x| 2^(56 - e) = M 2^sh < 2^56
-        F = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> -sh) : 0ull);
-    }
-    const uint32_t sg = (uint32_t)(b >> 48) & 0x8000u;
-#pragma unroll
-    for (int p = 0; p < OZP; ++p) {
-        const uint32_t v = (uint32_t)(F >> (49 - 7 * p)) & 127u;
-        const float f = __uint_as_float(0x4B000000u | v) - 8388608.0f;   // (float)v, exact
-        d[p] = (__float_as_uint(f) >> 16) | (v ? sg : 0u);              // BF16 bits, exact
-    }
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// an integer-valued float below 2^22 in magnitude, as int (exact)
-__device__ __forceinline__ long long oz_int(float v) {
-    return (long long)(__float_as_int(v + 12582912.0f) - 0x4B400000);
-}
-
-__global__ void __launch_bounds__(NT) k_schur_oz(SchurArgs A) {
+__global__ void __launch_bounds__(NT, 3) k_schur_oz(SchurArgs A) {
     HbScope hb_(5);
     const int lane = blockIdx.y;
     if (lane >= *A.active) return;
@@ -1002,46 +1056,29 @@ __global__ void __launch_bounds__(NT) k_schur_oz(SchurArgs A) {
     }
     const int i0 = (tile / A.tdim) * TS, j0 = (tile % A.tdim) * TS;
     if (i0 >= ra || j0 >= rb) return;
-    const double* W = scr + A.lay.w + (size_t)P.ta * D * D + (size_t)i0 * D;
-    const double* Y = scr + A.lay.y + (size_t)P.tb * D * D + (size_t)j0 * D;
+    const int dk = A.lay.dk;
+    const uint16_t* wd = reinterpret_cast<const uint16_t*>(scr + A.lay.wd) + (size_t)P.ta * OZP * D * dk;
+    const uint16_t* yd = reinterpret_cast<const uint16_t*>(scr + A.lay.yd) + (size_t)P.tb * OZP * D * dk;
+    const int* we = reinterpret_cast<const int*>(scr + A.lay.we) + P.ta * D;
+    const int* ye = reinterpret_cast<const int*>(scr + A.lay.ye) + P.tb * D;
     const int nr = min(TS, ra - i0), nc = min(TS, rb - j0);
     __shared__ __align__(16) uint16_t sA[OZP][TS][OZLD], sB[OZP][TS][OZLD];
-    __shared__ int sEa[TS], sEb[TS];
     const int w = threadIdx.x / 32, l = threadIdx.x % 32, gid = l / 4, tig = l % 4;
-    // row scales: the largest exponent of each row over all k
-    for (int r = w; r < TS; r += NT / 32) {
-        int ea = 0, eb = 0;
-        for (int k = l; k < Rp; k += 32) {
-            if (r < nr) ea = max(ea, oz_expo(W[(size_t)r * D + k]));
-            if (r < nc) eb = max(eb, oz_expo(Y[(size_t)r * D + k]));
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, o));
-            eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, o));
-        }
-        if (l == 0) { sEa[r] = ea; sEb[r] = eb; }
-    }
-    __syncthreads();
     // warp tile: rows 16 mi .. 16 mi + 15, columns 8 ni .. 8 ni + 7
     const int mi = w / 4, ni = w % 4;
     const bool act = 16 * mi < nr && 8 * ni < nc;      // warp-uniform
     long long hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
     for (int k0 = 0; k0 < Rp; k0 += OZK) {
         const int kc = min(OZK, Rp - k0);
-        // digits of this chunk: 2 operands x TS rows x OZK/2 pairs of k
-        for (int e = threadIdx.x; e < 2 * TS * (OZK / 2); e += NT) {
-            const int op = e / (TS * (OZK / 2)), rem = e % (TS * (OZK / 2));
-            const int r = rem / (OZK / 2), k = 2 * (rem % (OZK / 2));
-            const double* src = op ? Y : W;
-            const int nrow = op ? nc : nr, em = op ? sEb[r] : sEa[r];
-            const double x0 = (r < nrow && k < kc) ? src[(size_t)r * D + k0 + k] : 0.0;
-            const double x1 = (r < nrow && k + 1 < kc) ? src[(size_t)r * D + k0 + k + 1] : 0.0;
-            uint32_t d0[OZP], d1[OZP];
-            oz_digits(x0, em, d0);
-            oz_digits(x1, em, d1);
-            uint16_t (*dst)[TS][OZLD] = op ? sB : sA;
-#pragma unroll
-            for (int p = 0; p < OZP; ++p) *reinterpret_cast<uint32_t*>(&dst[p][r][k]) = d0[p] | (d1[p] << 16);
+        // digit chunk: 2 operands x OZP digits x TS rows x 4 segments of 8 k
+        for (int e = threadIdx.x; e < 2 * OZP * TS * 4; e += NT) {
+            const int op = e / (OZP * TS * 4), p = (e / (TS * 4)) % OZP, r = (e / 4) % TS, c = e % 4;
+            const int nrow = op ? nc : nr;
+            const uint16_t* src = op ? yd : wd;
+            const int row0 = op ? j0 : i0;
+            int4 v = make_int4(0, 0, 0, 0);
+            if (r < nrow) v = *reinterpret_cast<const int4*>(&src[((size_t)p * D + row0 + r) * dk + k0 + 8 * c]);
+            *reinterpret_cast<int4*>(op ? &sB[p][r][8 * c] : &sA[p][r][8 * c]) = v;
         }
         __syncthreads();
         if (act) {
@@ -1089,9 +1126,11 @@ __global__ void __launch_bounds__(NT) k_schur_oz(SchurArgs A) {
     for (int c = 0; c < 4; ++c) {
         const int r = 16 * mi + gid + (c >= 2 ? 8 : 0), q = 8 * ni + 2 * tig + (c & 1);
         if (r < nr && q < nc) {
-            const int e = (sEa[r] - 1022) + (sEb[q] - 1022);
+            const int e = (we[i0 + r] - 1022) + (ye[j0 + q] - 1022) - 35;
             const double v = fma((double)lo[c], 0x1p-28, (double)hi[c]);   // exact operands, one rounding
-            belem(B, D, P.trans, i0 + r, j0 + q) -= ldexp(v, e - 35);
+            const double sc = (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52)
+                                                        : ldexp(1.0, e);
+            belem(B, D, P.trans, i0 + r, j0 + q) -= v * sc;
         }
     }
 }
@@ -1467,7 +1506,7 @@ int alloc_workspace(h2_matrix* h, int lanes) {
             nrow_max = std::max(nrow_max, nn + nf);
             nfill_max = std::max(nfill_max, nf);
         }
-        W.lay = scratch_layout(D.dmax, nfill_max, ntarg_max);
+        W.lay = scratch_layout(D.dmax, nfill_max, ntarg_max, h->opt.precision == H2_PREC_FP64_TC);
         for (const auto& cl : lp.color_lists) W.ncl_max = std::max<int>(W.ncl_max, (int)cl.size());
         scratch_max = std::max(scratch_max, (size_t)W.ncl_max * lanes * W.lay.total);
         if (l < L) merge_max = std::max(merge_max, (size_t)D.nslots * lanes * 2 * D.dmax * D.dmax);
