@@ -67,7 +67,7 @@ FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 (profiling recipe table); not i
 # profiles/k_schur_laplace2d_n1024_256lanes.md; valid for that workload and lane
 # count while the kernel's source is unchanged (sha256 prefix of its text)
 NCU_TRAFFIC = {"kernel": "k_schur", "workload": "laplace2d_n1024", "lanes": 256,
-               "bytes_per_launch": None, "source_sha": None}
+               "bytes_per_launch": 323.73e6, "source_sha": "e262b9026709436a"}
 KERNEL_REGIONS = {"k_schur": ("h2_factor.cu", "struct SchurArgs {",
                                "// FP64-accurate Schur products on the tensor cores")}
 
@@ -538,11 +538,12 @@ SERVING_SIZES = (1024, 2048, 4096, 8192)
 def _serving_run(args, rate, seconds, seed):
     """One open-loop run on freshly built resident matrices (cold (mu, nu)
     tables): Poisson arrivals at `rate` for `seconds`."""
+    import paper_2311_08618_gb300 as pkg
     from paper_2311_08618_gb300 import serving
     srv = serving.Server()
     for i, n in enumerate(SERVING_SIZES):
         srv.add_matrix("m%d" % i, W.uniform_cube(n, 2, 100 + i), W.LAPLACE_EPS, (1e-3, 0, 0, 0), 64, 16,
-                       lanes=args.serving_lanes)
+                       lanes=args.serving_lanes, precision=pkg.H2_PREC_FP64_TC)
     u = W.uniform(seed, 4 * 100000)
     arr, t, j = [], 0.0, 0
     while True:
@@ -571,7 +572,7 @@ def _serving(args):
     tol log-uniform in [1e-10, 1e-6]) over resident 2D Laplace H^2 matrices of
     different sizes; continuous batching (paper_2311_08618_gb300.serving).  One
     run at the offered (overload) rate and one at a sustainable rate."""
-    res = {"matrices": "4 resident 2D Laplace H2 matrices n=%s (leaf 64, rank 16), %d lanes each, FP64"
+    res = {"matrices": "4 resident 2D Laplace H2 matrices n=%s (leaf 64, rank 16), %d lanes each, FP64_TC"
                        % (list(SERVING_SIZES), args.serving_lanes),
            "stand_in": "the 64-matrix 3D n<=131072 configuration needs ~16-70 GB per lane under eta=1 box "
                        "admissibility and does not fit one GPU"}
