@@ -152,6 +152,47 @@ int h2_inertia(h2_handle h, const double* shifts, int64_t ns, int64_t* counts,
 int h2_inertia_device(h2_handle h, const double* d_shifts, int64_t ns, int64_t* d_counts,
                       double* d_min_abs_pivot);
 
+/* ---- batches over several matrices (one launch per level and colour) ---- */
+typedef struct h2_group_set* h2_group;
+
+/*
+ * h2_group_create -- prepares one inertia batch over several resident
+ * matrices.  Every kernel of the generalized LDL^T (Sec. 3.2-3.4) runs as one
+ * launch per tree level, counted from the leaves, and per colour, covering the
+ * work of all handles.  Each block finds its matrix in a per-launch table.
+ * The batch is one CUDA graph.  The handles keep their own workspaces, so the
+ * counts equal those of each handle's own batch.
+ *   hs  : host, nh handles with equal max_lanes and precision, built on one
+ *         stream (the group's); they must outlive the group and must not run
+ *         their own batches while the group's is in flight.
+ *   *out: receives the group on success, untouched on failure.
+ * Errors: H2_ERR_INVALID_ARG (nh < 1, a null handle, mixed lanes or
+ * precision), H2_ERR_OOM, H2_ERR_CUDA.
+ */
+int h2_group_create(const h2_handle* hs, int nh, h2_group* out);
+
+/*
+ * h2_group_inertia_device -- the counts (and min |pivot|) of every handle's
+ * shifts, in one batch.  Enqueued on the group's stream; returns without
+ * waiting.
+ *   d_shifts        : device, nh * max_lanes FP64; handle i's shifts start at
+ *                     i * max_lanes.
+ *   ns              : host, nh ints in 0..max_lanes, the shifts of each handle.
+ *   d_counts        : device, nh * max_lanes int64, same layout (caller-owned).
+ *   d_min_abs_pivot : device, same layout FP64, or NULL.
+ * H2_PREC_MIXED handles return their mixed counts without the FP64 re-run,
+ * as h2_inertia_device does.  Errors: H2_ERR_INVALID_ARG, H2_ERR_CUDA.
+ */
+int h2_group_inertia_device(h2_group g, const double* d_shifts, const int* ns, int64_t* d_counts,
+                            double* d_min_abs_pivot);
+
+/* Launches (grouped kernels plus the per-handle bookkeeping kernels) of one
+ * group batch; < 0 for a NULL group. */
+int h2_group_launches(h2_group g);
+
+/* Frees the group (not its handles).  NULL is a no-op. */
+void h2_group_destroy(h2_group g);
+
 /* ---- k-th eigenvalues (Algorithm 1 with the inertia reuse of Sec. 4.2) ---- */
 /*
  * h2_kth_eig -- out[i] = lambda~_{k[i]} of A~, the midpoint of a final

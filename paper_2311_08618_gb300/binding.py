@@ -19,7 +19,8 @@ H2_PREC_FP64, H2_PREC_MIXED, H2_PREC_FP64_TC = 0, 1, 2
 
 EXPORTED_SYMBOLS = ["h2_default_options", "h2_build", "h2_destroy", "h2_last_error", "h2_inertia",
                     "h2_inertia_device", "h2_kth_eig", "h2_info", "h2_tree_perm", "h2_level_ranks",
-                    "h2_profile_batch", "h2_dense_inertia_noalloc", "h2_status", "h2_heartbeat"]
+                    "h2_profile_batch", "h2_dense_inertia_noalloc", "h2_status", "h2_heartbeat",
+                    "h2_group_create", "h2_group_inertia_device", "h2_group_launches", "h2_group_destroy"]
 KIND_NAMES = ["init", "recomp", "rotate", "ldl", "trsm", "schur", "merge", "other"]
 
 
@@ -85,6 +86,14 @@ def lib():
         L.h2_heartbeat.restype = None
         L.h2_status.argtypes = [P, P]
         L.h2_status.restype = C.c_int
+        L.h2_group_create.argtypes = [P, C.c_int, C.POINTER(P)]
+        L.h2_group_create.restype = C.c_int
+        L.h2_group_inertia_device.argtypes = [P, P, P, P, P]
+        L.h2_group_inertia_device.restype = C.c_int
+        L.h2_group_launches.argtypes = [P]
+        L.h2_group_launches.restype = C.c_int
+        L.h2_group_destroy.argtypes = [P]
+        L.h2_group_destroy.restype = None
         for f in ("h2_build", "h2_inertia", "h2_inertia_device", "h2_kth_eig", "h2_info",
                   "h2_tree_perm", "h2_level_ranks", "h2_profile_batch"):
             getattr(L, f).restype = C.c_int
@@ -194,3 +203,37 @@ class H2Matrix:
         r = np.zeros(1 << level, dtype=np.int32)
         _check(lib().h2_level_ranks(self._h, int(level), r.ctypes.data_as(C.c_void_p)))
         return r
+
+
+class H2Group:
+    """One inertia batch over several resident H2Matrix handles (h2_group_create
+    ... h2_group_destroy): one launch per tree level and colour for all of them.
+    The handles must share max_lanes, precision and stream, and stay alive."""
+
+    def __init__(self, mats):
+        self.mats = list(mats)
+        arr = (C.c_void_p * len(self.mats))(*[m._h.value for m in self.mats])
+        g = C.c_void_p()
+        _check(lib().h2_group_create(C.cast(arr, C.c_void_p), len(self.mats), C.byref(g)))
+        self._g = g
+
+    def close(self):
+        if getattr(self, "_g", None):
+            lib().h2_group_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launches(self) -> int:
+        return int(lib().h2_group_launches(self._g))
+
+    def h2_group_inertia_device(self, d_shifts, ns, d_counts, d_minpiv=None):
+        """d_shifts, d_counts (, d_minpiv): device buffers of len(mats) * max_lanes;
+        ns: shifts per handle (host sequence)."""
+        n = np.ascontiguousarray(ns, dtype=np.int32).ravel()
+        _check(lib().h2_group_inertia_device(self._g, _ptr(d_shifts), n.ctypes.data_as(C.c_void_p),
+                                             _ptr(d_counts), _ptr(d_minpiv)))

@@ -138,6 +138,25 @@ int h2_inertia_device(h2_handle h, const double* d_shifts, int64_t ns, int64_t* 
     return run_inertia(h, d_shifts, (int)ns, d_counts, d_min_abs_pivot);
 }
 
+int h2_group_create(const h2_handle* hs, int nh, h2_group* out) {
+    g_last_error.clear();
+    if (!hs || !out || nh < 1) { set_error("h2_group_create: bad arguments"); return H2_ERR_INVALID_ARG; }
+    for (int i = 0; i < nh; ++i)
+        if (!hs[i]) { set_error("h2_group_create: null handle"); return H2_ERR_INVALID_ARG; }
+    return group_create(hs, nh, out);
+}
+
+int h2_group_inertia_device(h2_group g, const double* d_shifts, const int* ns, int64_t* d_counts,
+                            double* d_min_abs_pivot) {
+    g_last_error.clear();
+    if (!g || !d_shifts || !ns || !d_counts) { set_error("h2_group_inertia_device: bad arguments"); return H2_ERR_INVALID_ARG; }
+    return group_inertia(g, d_shifts, ns, d_counts, d_min_abs_pivot);
+}
+
+int h2_group_launches(h2_group g) { return g ? group_launches(g) : -1; }
+
+void h2_group_destroy(h2_group g) { group_destroy(g); }
+
 int h2_kth_eig(h2_handle h, const int64_t* k, int64_t nk, double tol, double* out, double* err_bound) {
     g_last_error.clear();
     if (!h || nk < 0 || (nk > 0 && (!k || !out)) || !(tol > 0.0)) { set_error("h2_kth_eig: bad arguments"); return H2_ERR_INVALID_ARG; }

@@ -19,6 +19,8 @@
 // and applies the transfer bases (Sec. 3.3).  The whole sequence is captured
 // once into a CUDA graph and replayed per batch.
 #include <algorithm>
+#include <functional>
+#include <tuple>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -194,10 +196,33 @@ __device__ __noinline__ void report_bad(int* err, int kernel, int a, int b, int 
 // [4] recompression ran, [8 + ti] live rows of target ti
 constexpr int HDR_ROWS = 8;
 
+// Multi-matrix (grouped) launches.  A grouped launch runs one kernel over the
+// work of several handles: item m (a handle's level and colour) owns the
+// blockIdx.x range [off[m], off[m+1]) and its own argument struct; flag[m]
+// carries the item's shared-memory switch where the kernel has one.  The
+// kernel bodies take their block coordinates as arguments, so the single and
+// the grouped launches execute the same code.
+template <typename Args>
+struct GroupArgs {
+    const Args* args;
+    const int* off;      // n + 1 prefix offsets of blockIdx.x
+    const int* flag;     // per item (may be null)
+    int n;
+};
+
+__device__ __forceinline__ int group_find(const int* off, int n, int bx) {
+    int lo = 0, hi = n - 1;                      // largest m with off[m] <= bx
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= bx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // ---- (i) recompression basis of row p (Sec. 3.4): one CTA per (cluster, lane)
-__global__ void __launch_bounds__(NT) k_recomp(FactorArgs A) {
+__device__ __forceinline__ void k_recomp_body(const FactorArgs& A, const int bx, const int by) {
     HbScope hb_(1);
-    const int ci = blockIdx.x, lane = blockIdx.y;
+    const int ci = bx, lane = by;
     if (lane >= *A.active) return;
     __shared__ double red[32];
     __shared__ int redi[32];
@@ -258,6 +283,11 @@ __global__ void __launch_bounds__(NT) k_recomp(FactorArgs A) {
         A.rk[p * LN + lane] = r0 + t;
         if (s_bad) atomicOr(A.err, 1);
     }
+}
+__global__ void __launch_bounds__(NT) k_recomp(FactorArgs A) { k_recomp_body(A, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(NT) k_recomp_g(GroupArgs<FactorArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_recomp_body(G.args[m], blockIdx.x - G.off[m], blockIdx.y);
 }
 
 // ---- (i') the same recompression for wide fill rows: one thread-block
@@ -384,11 +414,11 @@ __device__ int cluster_pivqr(cg::cluster_group& cl, int g, double* Y, int ldy, i
     return k;
 }
 
-__global__ void __cluster_dims__(QG, 1, 1) __launch_bounds__(NT) k_recomp_cluster(FactorArgs A) {
+__device__ __forceinline__ void k_recomp_cluster_body(const FactorArgs& A, const int bx, const int by) {
     HbScope hb_(1);
     cg::cluster_group cl = cg::this_cluster();
     const int g = (int)cl.block_rank();
-    const int ci = blockIdx.x / QG, lane = blockIdx.y;
+    const int ci = bx / QG, lane = by;
     // every early return below depends on (ci, lane) only: taken by the whole cluster
     if (lane >= *A.active) return;
     extern __shared__ double sv[];       // reflector, D doubles
@@ -455,6 +485,14 @@ __global__ void __cluster_dims__(QG, 1, 1) __launch_bounds__(NT) k_recomp_cluste
         A.rk[p * LN + lane] = r0 + t;
         if (s_bad) atomicOr(A.err, 1);
     }
+}
+__global__ void __cluster_dims__(QG, 1, 1) __launch_bounds__(NT) k_recomp_cluster(FactorArgs A) {
+    k_recomp_cluster_body(A, blockIdx.x, blockIdx.y);
+}
+// item offsets are multiples of QG, so a cluster never spans two items
+__global__ void __cluster_dims__(QG, 1, 1) __launch_bounds__(NT) k_recomp_cluster_g(GroupArgs<FactorArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_recomp_cluster_body(G.args[m], blockIdx.x - G.off[m], blockIdx.y);
 }
 
 // ---- (ii) rotation of p's redundant coordinates in one block of row p and
@@ -578,9 +616,9 @@ __host__ __device__ constexpr size_t rotate_smem(int D) {
 
 // NU = rotate_nu(D) of the level (R <= D; rows beyond 8 * NU take more passes)
 template <typename T, int NU>
-__global__ void __launch_bounds__(NT) k_rotate(FactorArgs A) {
+__device__ __forceinline__ void k_rotate_body(const FactorArgs& A, const int bx, const int by) {
     HbScope hb_(2);
-    const int ci = blockIdx.x / A.nrow_max, b = blockIdx.x % A.nrow_max, lane = blockIdx.y;
+    const int ci = bx / A.nrow_max, b = bx % A.nrow_max, lane = by;
     if (lane >= *A.active || b >= A.nrow[ci]) return;
     extern __shared__ __align__(16) unsigned char rot_smem[];
     const int D = A.D, LN = A.lanes;
@@ -624,12 +662,19 @@ __global__ void __launch_bounds__(NT) k_rotate(FactorArgs A) {
     }
     if (threadIdx.x == 0 && fl > 0.0) add_stats(A.stats, H2_KIND_ROTATE, fl, 8.0 * fl / R);
 }
+template <typename T, int NU>
+__global__ void __launch_bounds__(NT) k_rotate(FactorArgs A) { k_rotate_body<T, NU>(A, blockIdx.x, blockIdx.y); }
+template <typename T, int NU>
+__global__ void __launch_bounds__(NT) k_rotate_g(GroupArgs<FactorArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_rotate_body<T, NU>(G.args[m], blockIdx.x - G.off[m], blockIdx.y);
+}
 
 // FP64 path: one output per thread and step over the exact R x nj outputs of
 // each pass (no padded rows or columns: every DFMA is algorithmic)
-__global__ void __launch_bounds__(NT) k_rotate_fp64(FactorArgs A) {
+__device__ __forceinline__ void k_rotate_fp64_body(const FactorArgs& A, const int bx, const int by) {
     HbScope hb_(2);
-    const int ci = blockIdx.x / A.nrow_max, b = blockIdx.x % A.nrow_max, lane = blockIdx.y;
+    const int ci = bx / A.nrow_max, b = bx % A.nrow_max, lane = by;
     if (lane >= *A.active || b >= A.nrow[ci]) return;
     extern __shared__ double tile[];          // R x RC
     const int D = A.D, LN = A.lanes;
@@ -700,13 +745,18 @@ __global__ void __launch_bounds__(NT) k_rotate_fp64(FactorArgs A) {
     }
     if (threadIdx.x == 0 && fl > 0.0) add_stats(A.stats, H2_KIND_ROTATE, fl, 8.0 * fl / R);
 }
+__global__ void __launch_bounds__(NT) k_rotate_fp64(FactorArgs A) { k_rotate_fp64_body(A, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(NT) k_rotate_fp64_g(GroupArgs<FactorArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_rotate_fp64_body(G.args[m], blockIdx.x - G.off[m], blockIdx.y);
+}
 
 // ---- (iii) Bunch-Kaufman LDL^T of S_pp^RR (Eq. blr2-diag-ldl) and its
 // negative-pivot count: one CTA per (cluster, lane)
 template <int NTH>
-__global__ void __launch_bounds__(NTH) k_ldl(FactorArgs A, int use_smem) {
+__device__ __forceinline__ void k_ldl_body(const FactorArgs& A, const int use_smem, const int bx, const int by) {
     HbScope hb_(3);
-    const int ci = blockIdx.x, lane = blockIdx.y;
+    const int ci = bx, lane = by;
     if (lane >= *A.active) return;
     extern __shared__ double sF[];
     __shared__ double red[32];
@@ -762,6 +812,13 @@ __global__ void __launch_bounds__(NTH) k_ldl(FactorArgs A, int use_smem) {
         add_stats(A.stats, H2_KIND_LDL, (double)Rp * Rp * Rp / 3.0, 16.0 * (double)Rp * Rp);
     }
 }
+template <int NTH>
+__global__ void __launch_bounds__(NTH) k_ldl(FactorArgs A, int use_smem) { k_ldl_body<NTH>(A, use_smem, blockIdx.x, blockIdx.y); }
+template <int NTH>
+__global__ void __launch_bounds__(NTH) k_ldl_g(GroupArgs<FactorArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_ldl_body<NTH>(G.args[m], G.flag[m], blockIdx.x - G.off[m], blockIdx.y);
+}
 
 // Digits of the FP64_TC Schur products (see k_schur_oz).
 constexpr int OZP = 8;
@@ -814,9 +871,9 @@ constexpr int JB = 8;
 // (FP64 path) or float (mixed path: the FP64 factor L, D of the LDL step is
 // rounded to FP32, as are the products that form the Schur update)
 template <typename T>
-__global__ void __launch_bounds__(NT) k_trsm(FactorArgs A, int use_smem) {
+__device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_smem, const int bx, const int by) {
     HbScope hb_(4);
-    const int ci = blockIdx.x / A.ntarg_max, ti = blockIdx.x % A.ntarg_max, lane = blockIdx.y;
+    const int ci = bx / A.ntarg_max, ti = bx % A.ntarg_max, lane = by;
     if (lane >= *A.active || ti >= A.ntarg[ci]) return;
     extern __shared__ double sh[];
     const int D = A.D, LN = A.lanes;
@@ -957,6 +1014,13 @@ __global__ void __launch_bounds__(NT) k_trsm(FactorArgs A, int use_smem) {
         }
     }
 }
+template <typename T>
+__global__ void __launch_bounds__(NT) k_trsm(FactorArgs A, int use_smem) { k_trsm_body<T>(A, use_smem, blockIdx.x, blockIdx.y); }
+template <typename T>
+__global__ void __launch_bounds__(NT) k_trsm_g(GroupArgs<FactorArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_trsm_body<T>(G.args[m], G.flag[m], blockIdx.x - G.off[m], blockIdx.y);
+}
 
 struct SchurArgs {
     double* slots;
@@ -974,11 +1038,11 @@ struct SchurArgs {
 // path) or float (mixed path: FP32 products and accumulation, the FP64 block
 // updated by the rounded result).
 template <typename T>
-__global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
+__device__ __forceinline__ void k_schur_body(const SchurArgs& A, const int bx, const int by) {
     HbScope hb_(5);
-    const int lane = blockIdx.y;
+    const int lane = by;
     if (lane >= *A.active) return;
-    const int pi = blockIdx.x / A.tiles_per_pair, tile = blockIdx.x % A.tiles_per_pair;
+    const int pi = bx / A.tiles_per_pair, tile = bx % A.tiles_per_pair;
     const SchurPair P = A.pairs[pi];
     const int D = A.D;
     const double* scr = A.scratch + ((size_t)P.elim * A.lanes + lane) * A.lay.total;
@@ -1020,6 +1084,13 @@ __global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
         if (i < ra && j < rb) belem(B, D, P.trans, i, j) -= (double)acc[u];
     }
 }
+template <typename T>
+__global__ void __launch_bounds__(NT) k_schur(SchurArgs A) { k_schur_body<T>(A, blockIdx.x, blockIdx.y); }
+template <typename T>
+__global__ void __launch_bounds__(NT) k_schur_g(GroupArgs<SchurArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_schur_body<T>(G.args[m], blockIdx.x - G.off[m], blockIdx.y);
+}
 
 // FP64-accurate Schur products on the tensor cores (precision H2_PREC_FP64_TC).
 // Every row of W (and of Y) is scaled by 2^e with |x| < 2^e over the row and
@@ -1038,11 +1109,11 @@ __global__ void __launch_bounds__(NT) k_schur(SchurArgs A) {
 // hi 2^-35 + lo 2^-63.  (Splitting FP64 operands into small-integer slices
 // whose products a low-precision unit sums exactly is the scheme of Ozaki,
 // Ogita, Oishi and Rump, 2012.)
-__global__ void __launch_bounds__(NT, 3) k_schur_oz(SchurArgs A) {
+__device__ __forceinline__ void k_schur_oz_body(const SchurArgs& A, const int bx, const int by) {
     HbScope hb_(5);
-    const int lane = blockIdx.y;
+    const int lane = by;
     if (lane >= *A.active) return;
-    const int pi = blockIdx.x / A.tiles_per_pair, tile = blockIdx.x % A.tiles_per_pair;
+    const int pi = bx / A.tiles_per_pair, tile = bx % A.tiles_per_pair;
     const SchurPair P = A.pairs[pi];
     const int D = A.D;
     const double* scr = A.scratch + ((size_t)P.elim * A.lanes + lane) * A.lay.total;
@@ -1134,6 +1205,11 @@ __global__ void __launch_bounds__(NT, 3) k_schur_oz(SchurArgs A) {
         }
     }
 }
+__global__ void __launch_bounds__(NT, 3) k_schur_oz(SchurArgs A) { k_schur_oz_body(A, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(NT, 3) k_schur_oz_g(GroupArgs<SchurArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_schur_oz_body(G.args[m], blockIdx.x - G.off[m], blockIdx.y);
+}
 
 // Mixed path: S_ab[i0:i0+64, j0:j0+64] -= W_a Y_b^T (Eq. blr2-diag-schur) with
 // FP32 products and accumulation; W, Y were stored in FP32 by k_trsm<float>.
@@ -1141,11 +1217,11 @@ __global__ void __launch_bounds__(NT, 3) k_schur_oz(SchurArgs A) {
 // reads are warp broadcasts, the Y reads hit 16 distinct banks, and the FP64
 // read-modify-write of S is coalesced along rows.
 constexpr int TSF = 64;
-__global__ void __launch_bounds__(NT) k_schur_f32(SchurArgs A) {
+__device__ __forceinline__ void k_schur_f32_body(const SchurArgs& A, const int bx, const int by) {
     HbScope hb_(5);
-    const int lane = blockIdx.y;
+    const int lane = by;
     if (lane >= *A.active) return;
-    const int pi = blockIdx.x / A.tiles_per_pair, tile = blockIdx.x % A.tiles_per_pair;
+    const int pi = bx / A.tiles_per_pair, tile = bx % A.tiles_per_pair;
     const SchurPair P = A.pairs[pi];
     const int D = A.D;
     const double* scr = A.scratch + ((size_t)P.elim * A.lanes + lane) * A.lay.total;
@@ -1199,6 +1275,11 @@ __global__ void __launch_bounds__(NT) k_schur_f32(SchurArgs A) {
             if (r < ra && c < rb) belem(B, D, P.trans, r, c) -= (double)acc[i][j];
         }
 }
+__global__ void __launch_bounds__(NT) k_schur_f32(SchurArgs A) { k_schur_f32_body(A, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(NT) k_schur_f32_g(GroupArgs<SchurArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_schur_f32_body(G.args[m], blockIdx.x - G.off[m], blockIdx.y);
+}
 
 // leaf level: copy Q^T A Q near blocks, subtract sigma on the diagonal, fill
 // blocks start as their coupling; dims/ranks from the build
@@ -1218,9 +1299,9 @@ struct InitArgs {
     double* stats;
 };
 
-__global__ void k_init_leaf(InitArgs A) {
+__device__ __forceinline__ void k_init_leaf_body(const InitArgs& A, const int bx, const int by) {
     HbScope hb_(0);
-    const int sl = blockIdx.x, lane = blockIdx.y;
+    const int sl = bx, lane = by;
     if (lane >= *A.active) return;
     const int D = A.D;
     double* B = slot_ptr(A.slots, sl, A.lanes, lane, D);
@@ -1242,6 +1323,11 @@ __global__ void k_init_leaf(InitArgs A) {
             B[e] = (i < ra && j < rbb) ? C[(size_t)i * A.rbl + j] : 0.0;
         }
     }
+}
+__global__ void k_init_leaf(InitArgs A) { k_init_leaf_body(A, blockIdx.x, blockIdx.y); }
+__global__ void k_init_leaf_g(GroupArgs<InitArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_init_leaf_body(G.args[m], blockIdx.x - G.off[m], blockIdx.y);
 }
 
 __global__ void k_init_dims(int* dim, int* rk, const int64_t* off, const int* rb, int nc, int lanes,
@@ -1304,9 +1390,9 @@ __device__ __forceinline__ int place_child(int first, int i, int rb_self, int rb
     return rb1 + rb2 + (first ? (i - rb_self) : t1 + (i - rb_self));
 }
 
-__global__ void __launch_bounds__(NT) k_merge(MergeArgs A) {
+__device__ __forceinline__ void k_merge_body(const MergeArgs& A, const int bx, const int by) {
     HbScope hb_(6);
-    const int sl = blockIdx.x, lane = blockIdx.y;
+    const int sl = bx, lane = by;
     if (lane >= *A.active) return;
     const int DP = A.DP, LN = A.lanes;
     double* out = slot_ptr(A.slotsP, sl, LN, lane, DP);
@@ -1396,6 +1482,11 @@ __global__ void __launch_bounds__(NT) k_merge(MergeArgs A) {
         }
         out[e] = v;
     }
+}
+__global__ void __launch_bounds__(NT) k_merge(MergeArgs A) { k_merge_body(A, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(NT) k_merge_g(GroupArgs<MergeArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_merge_body(G.args[m], blockIdx.x - G.off[m], blockIdx.y);
 }
 
 __global__ void k_set_int(int* p, int v) {
@@ -1639,31 +1730,70 @@ struct Profiler {
 
 // enqueue one full factorization of the workspace's lanes on stream st;
 // returns the number of kernel launches
-static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, int mixed) {
+// One launch of a batch, described before it is launched, so that a single
+// handle launches its records one by one and a group of handles merges the
+// records of equal key (step, colour, operation, variant) into one grouped
+// launch (h2_group).  The 1-D bookkeeping kernels are kept as closures.
+enum Op {
+    OP_INIT_DIMS, OP_INIT_LEAF, OP_RECOMP, OP_RECOMP_CL, OP_ROTATE, OP_LDL, OP_TRSM, OP_SCHUR,
+    OP_MERGE_DIMS, OP_MERGE, OP_FINISH
+};
+
+struct LaunchRec {
+    int op = 0, kind = 0;
+    int phase = 0, step = 0, colour = 0;   // order key across handles
+    int variant = 0;                       // template choice (see launch_single)
+    dim3 grid;
+    int block = NT;
+    size_t smem = 0;
+    int flag = 0;
+    FactorArgs fa{};
+    SchurArgs sa{};
+    InitArgs ia{};
+    MergeArgs ma{};
+    std::function<void(cudaStream_t)> tiny;
+};
+
+static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
+    std::vector<LaunchRec> R;
     const Plan& P = h->plan;
     const int L = P.L;
     Workspace& ws = h->ws;
     FactorState* fs = state_of(h);
     const int LN = ws.lanes;
-    int nl = 0;
-    auto B = [&](int k) { ++nl; if (prof) prof->before(k); };
-    auto E = [&]() { if (prof) prof->after(); };
     {
         LevelDev& D = h->lev[L];
-        int ne = std::max(std::max(D.nc * LN, LN), 2 * H2_NKINDS);
-        B(H2_KIND_OTHER);
-        k_init_dims<<<(ne + 255) / 256, 256, 0, st>>>(ws.d_dim[L], ws.d_rk[L], D.d_off, D.d_rb, D.nc, LN,
-                                                     ws.d_neg, ws.d_minpiv, ws.d_err, fs->d_stats);
-        E();
-        InitArgs ia{ws.d_slots[L], D.dmax, LN, D.d_near_static, D.d_slot_a, D.d_slot_b, D.d_slot_kind,
-                    D.d_slot_far, D.d_C, D.estride, D.d_rb, ws.d_shifts, fs->d_active, fs->d_stats};
-        B(H2_KIND_INIT);
-        k_init_leaf<<<dim3(D.nslots, LN), NT, 0, st>>>(ia);
-        E();
+        const int ne = std::max(std::max(D.nc * LN, LN), 2 * H2_NKINDS);
+        LaunchRec r;
+        r.op = OP_INIT_DIMS;
+        r.kind = H2_KIND_OTHER;
+        r.phase = 0;
+        int* dim = ws.d_dim[L];
+        int* rk = ws.d_rk[L];
+        const int64_t* off = D.d_off;
+        const int* rb = D.d_rb;
+        const int nc = D.nc;
+        unsigned long long* neg = ws.d_neg;
+        unsigned long long* mp = ws.d_minpiv;
+        int* err = ws.d_err;
+        double* stats = fs->d_stats;
+        r.tiny = [=](cudaStream_t st) {
+            k_init_dims<<<(ne + 255) / 256, 256, 0, st>>>(dim, rk, off, rb, nc, LN, neg, mp, err, stats);
+        };
+        R.push_back(r);
+        LaunchRec q;
+        q.op = OP_INIT_LEAF;
+        q.kind = H2_KIND_INIT;
+        q.phase = 1;
+        q.ia = InitArgs{ws.d_slots[L], D.dmax, LN, D.d_near_static, D.d_slot_a, D.d_slot_b, D.d_slot_kind,
+                        D.d_slot_far, D.d_C, D.estride, D.d_rb, ws.d_shifts, fs->d_active, fs->d_stats};
+        q.grid = dim3(D.nslots, LN);
+        R.push_back(q);
     }
     for (int l = L; l >= 0; --l) {
         LevelDev& D = h->lev[l];
         LevelWork& W = fs->lw[l];
+        const int Dm = D.dmax;
         for (int c = 0; c < (int)W.colours.size(); ++c) {
             const ColourDev& C = W.colours[c];
             FactorArgs fa{ws.d_slots[l], D.dmax, LN, ws.d_dim[l], ws.d_rk[l], D.d_color, c, C.cl, C.targ,
@@ -1671,76 +1801,373 @@ static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, 
                           C.rowblk_trans, C.rowblk_fill, C.nrow, C.nrow_max, C.fillq, C.fillslot, C.nfill,
                           C.nfill_max, ws.d_scratch, W.lay, h->tol, 2.220446049250313e-16 * h->norm_inf,
                           h->fill_cap_eff, ws.d_neg, ws.d_minpiv, ws.d_err, fs->d_active, fs->d_stats};
-            const int Dm = D.dmax;
+            LaunchRec r;
+            r.phase = 2;
+            r.step = L - l;
+            r.colour = c;
+            r.fa = fa;
             if (C.has_fill) {
-                B(H2_KIND_RECOMP);
                 const int wide = h->opt.recomp_cluster_cols;
-                if (wide >= 0 && (size_t)C.nfill_max * Dm >= (wide > 0 ? (size_t)wide : kWideFill))
-                    k_recomp_cluster<<<dim3(C.ncl * QG, LN), NT, (size_t)Dm * sizeof(double), st>>>(fa);
-                else
-                    k_recomp<<<dim3(C.ncl, LN), NT, 0, st>>>(fa);
-                E();
-                B(H2_KIND_ROTATE);
-                const dim3 grid(C.ncl * C.nrow_max, LN);
-                const size_t sm = rotate_smem<float>(Dm);
-                if (!mixed)
-                    k_rotate_fp64<<<grid, NT, (size_t)Dm * RC * sizeof(double), st>>>(fa);
-                else if (rotate_nu(Dm) == 8)
-                    k_rotate<float, 8><<<grid, NT, sm, st>>>(fa);
-                else if (rotate_nu(Dm) == 16)
-                    k_rotate<float, 16><<<grid, NT, sm, st>>>(fa);
-                else
-                    k_rotate<float, 32><<<grid, NT, sm, st>>>(fa);
-                E();
+                LaunchRec q = r;
+                q.kind = H2_KIND_RECOMP;
+                if (wide >= 0 && (size_t)C.nfill_max * Dm >= (wide > 0 ? (size_t)wide : kWideFill)) {
+                    q.op = OP_RECOMP_CL;
+                    q.grid = dim3(C.ncl * QG, LN);
+                    q.smem = (size_t)Dm * sizeof(double);
+                } else {
+                    q.op = OP_RECOMP;
+                    q.grid = dim3(C.ncl, LN);
+                }
+                R.push_back(q);
+                q = r;
+                q.op = OP_ROTATE;
+                q.kind = H2_KIND_ROTATE;
+                q.grid = dim3(C.ncl * C.nrow_max, LN);
+                if (!mixed) {
+                    q.variant = 0;
+                    q.smem = (size_t)Dm * RC * sizeof(double);
+                } else {
+                    q.variant = rotate_nu(Dm);
+                    q.smem = rotate_smem<float>(Dm);
+                }
+                R.push_back(q);
             }
-            const size_t sm_ldl = ((size_t)Dm * Dm + 4 * (size_t)Dm) * sizeof(double);
-            const int ldl_smem = sm_ldl <= kSmemCap ? 1 : 0;
-            B(H2_KIND_LDL);
-            if (Dm <= 64)
-                k_ldl<128><<<dim3(C.ncl, LN), 128, ldl_smem ? sm_ldl : 0, st>>>(fa, ldl_smem);
-            else
-                k_ldl<NT><<<dim3(C.ncl, LN), NT, ldl_smem ? sm_ldl : 0, st>>>(fa, ldl_smem);
-            E();
-            const size_t sm_trsm = (size_t)Dm * Dm * sizeof(double) + 2 * (size_t)Dm * sizeof(int);
-            const int trsm_smem = sm_trsm <= kSmemCap ? 1 : 0;
-            B(H2_KIND_TRSM);
-            if (mixed)
-                k_trsm<float><<<dim3(C.ncl * C.ntarg_max, LN), NT, trsm_smem ? sm_trsm : 0, st>>>(fa, trsm_smem);
-            else
-                k_trsm<double><<<dim3(C.ncl * C.ntarg_max, LN), NT, trsm_smem ? sm_trsm : 0, st>>>(fa, trsm_smem);
-            E();
-            const int tdim = (D.dmax + (mixed ? TSF : TS) - 1) / (mixed ? TSF : TS);
-            SchurArgs sa{ws.d_slots[l], D.dmax, LN, C.pairs, tdim * tdim, tdim, ws.d_scratch, W.lay,
-                         fs->d_active, ws.d_err};
-            B(H2_KIND_SCHUR);
-            if (mixed)
-                k_schur_f32<<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
-            else if (h->opt.precision == H2_PREC_FP64_TC)
-                k_schur_oz<<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
-            else
-                k_schur<double><<<dim3(C.npairs * tdim * tdim, LN), NT, 0, st>>>(sa);
-            E();
+            {
+                const size_t sm_ldl = ((size_t)Dm * Dm + 4 * (size_t)Dm) * sizeof(double);
+                LaunchRec q = r;
+                q.op = OP_LDL;
+                q.kind = H2_KIND_LDL;
+                q.flag = sm_ldl <= kSmemCap ? 1 : 0;
+                q.variant = Dm <= 64 ? 128 : NT;
+                q.block = q.variant;
+                q.smem = q.flag ? sm_ldl : 0;
+                q.grid = dim3(C.ncl, LN);
+                R.push_back(q);
+            }
+            {
+                const size_t sm_trsm = (size_t)Dm * Dm * sizeof(double) + 2 * (size_t)Dm * sizeof(int);
+                LaunchRec q = r;
+                q.op = OP_TRSM;
+                q.kind = H2_KIND_TRSM;
+                q.flag = sm_trsm <= kSmemCap ? 1 : 0;
+                q.variant = mixed ? 1 : 0;
+                q.smem = q.flag ? sm_trsm : 0;
+                q.grid = dim3(C.ncl * C.ntarg_max, LN);
+                R.push_back(q);
+            }
+            {
+                const int ts = mixed ? TSF : TS;
+                const int tdim = (D.dmax + ts - 1) / ts;
+                LaunchRec q = r;
+                q.op = OP_SCHUR;
+                q.kind = H2_KIND_SCHUR;
+                q.sa = SchurArgs{ws.d_slots[l], D.dmax, LN, C.pairs, tdim * tdim, tdim, ws.d_scratch, W.lay,
+                                 fs->d_active, ws.d_err};
+                q.variant = mixed ? 1 : (h->opt.precision == H2_PREC_FP64_TC ? 2 : 0);
+                q.grid = dim3(C.npairs * tdim * tdim, LN);
+                R.push_back(q);
+            }
         }
         if (l > 0) {
             LevelDev& Pd = h->lev[l - 1];
-            int ne = Pd.nc * LN;
-            B(H2_KIND_OTHER);
-            k_merge_dims<<<(ne + 255) / 256, 256, 0, st>>>(ws.d_dim[l - 1], ws.d_rk[l - 1], ws.d_rk[l], Pd.d_rb,
-                                                          Pd.nc, LN);
-            E();
-            MergeArgs ma{ws.d_slots[l - 1], Pd.dmax, LN, Pd.d_slot_a, Pd.d_slot_b, Pd.d_slot_kind,
-                         Pd.d_slot_far, Pd.d_C, Pd.estride, Pd.d_rb, Pd.d_Q, Pd.dq, ws.d_slots[l], D.dmax,
-                         D.nc, W.d_slot_of, W.d_far_of, D.d_C, D.estride, D.d_rb, ws.d_rk[l], ws.d_merge,
-                         fs->d_active, fs->d_stats, ws.d_err};
-            B(H2_KIND_MERGE);
-            k_merge<<<dim3(Pd.nslots, LN), NT, 0, st>>>(ma);
-            E();
+            LaunchRec q;
+            q.phase = 2;
+            q.step = L - l;
+            q.colour = 1 << 20;          // after every colour of the step
+            q.op = OP_MERGE_DIMS;
+            q.kind = H2_KIND_OTHER;
+            const int ne = Pd.nc * LN;
+            int* dimP = ws.d_dim[l - 1];
+            int* rkP = ws.d_rk[l - 1];
+            const int* rkC = ws.d_rk[l];
+            const int* rbP = Pd.d_rb;
+            const int ncP = Pd.nc;
+            q.tiny = [=](cudaStream_t st) {
+                k_merge_dims<<<(ne + 255) / 256, 256, 0, st>>>(dimP, rkP, rkC, rbP, ncP, LN);
+            };
+            R.push_back(q);
+            LaunchRec m;
+            m.phase = 2;
+            m.step = L - l;
+            m.colour = 1 << 20;
+            m.op = OP_MERGE;
+            m.kind = H2_KIND_MERGE;
+            m.ma = MergeArgs{ws.d_slots[l - 1], Pd.dmax, LN, Pd.d_slot_a, Pd.d_slot_b, Pd.d_slot_kind,
+                             Pd.d_slot_far, Pd.d_C, Pd.estride, Pd.d_rb, Pd.d_Q, Pd.dq, ws.d_slots[l], D.dmax,
+                             D.nc, W.d_slot_of, W.d_far_of, D.d_C, D.estride, D.d_rb, ws.d_rk[l], ws.d_merge,
+                             fs->d_active, fs->d_stats, ws.d_err};
+            m.grid = dim3(Pd.nslots, LN);
+            R.push_back(m);
         }
     }
-    B(H2_KIND_OTHER);
-    k_finish<<<(LN + 255) / 256, 256, 0, st>>>(ws.d_neg, ws.d_minpiv, fs->d_counts, fs->d_mp, fs->d_active);
-    E();
+    LaunchRec f;
+    f.phase = 3;
+    f.op = OP_FINISH;
+    f.kind = H2_KIND_OTHER;
+    unsigned long long* neg = ws.d_neg;
+    unsigned long long* mp = ws.d_minpiv;
+    int64_t* counts = fs->d_counts;
+    double* dmp = fs->d_mp;
+    int* act = fs->d_active;
+    f.tiny = [=](cudaStream_t st) { k_finish<<<(LN + 255) / 256, 256, 0, st>>>(neg, mp, counts, dmp, act); };
+    R.push_back(f);
+    return R;
+}
+
+static void launch_single(const LaunchRec& r, cudaStream_t st) {
+    switch (r.op) {
+        case OP_INIT_LEAF: k_init_leaf<<<r.grid, NT, 0, st>>>(r.ia); break;
+        case OP_RECOMP: k_recomp<<<r.grid, NT, 0, st>>>(r.fa); break;
+        case OP_RECOMP_CL: k_recomp_cluster<<<r.grid, NT, r.smem, st>>>(r.fa); break;
+        case OP_ROTATE:
+            if (r.variant == 0) k_rotate_fp64<<<r.grid, NT, r.smem, st>>>(r.fa);
+            else if (r.variant == 8) k_rotate<float, 8><<<r.grid, NT, r.smem, st>>>(r.fa);
+            else if (r.variant == 16) k_rotate<float, 16><<<r.grid, NT, r.smem, st>>>(r.fa);
+            else k_rotate<float, 32><<<r.grid, NT, r.smem, st>>>(r.fa);
+            break;
+        case OP_LDL:
+            if (r.variant == 128) k_ldl<128><<<r.grid, 128, r.smem, st>>>(r.fa, r.flag);
+            else k_ldl<NT><<<r.grid, NT, r.smem, st>>>(r.fa, r.flag);
+            break;
+        case OP_TRSM:
+            if (r.variant) k_trsm<float><<<r.grid, NT, r.smem, st>>>(r.fa, r.flag);
+            else k_trsm<double><<<r.grid, NT, r.smem, st>>>(r.fa, r.flag);
+            break;
+        case OP_SCHUR:
+            if (r.variant == 1) k_schur_f32<<<r.grid, NT, 0, st>>>(r.sa);
+            else if (r.variant == 2) k_schur_oz<<<r.grid, NT, 0, st>>>(r.sa);
+            else k_schur<double><<<r.grid, NT, 0, st>>>(r.sa);
+            break;
+        case OP_MERGE: k_merge<<<r.grid, NT, 0, st>>>(r.ma); break;
+        default: r.tiny(st); break;
+    }
+}
+
+static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, int mixed) {
+    int nl = 0;
+    for (const LaunchRec& r : factor_records(h, mixed)) {
+        ++nl;
+        if (prof) prof->before(r.kind);
+        launch_single(r, st);
+        if (prof) prof->after();
+    }
     return nl;
+}
+
+// ------------------------------------------------------------ groups --
+// A group runs one batch for several handles: records of equal key from all
+// handles become one grouped launch (GroupArgs tables), so every level
+// (counted from the leaves) and colour is one launch over all matrices.
+struct GLaunch {
+    int op = 0, variant = 0, block = NT;
+    size_t smem = 0;
+    unsigned gx = 0, gy = 0;
+    void* d_args = nullptr;
+    int* d_off = nullptr;
+    int* d_flag = nullptr;
+    int n = 0;
+    std::vector<const LaunchRec*> tiny;
+};
+
+}  // namespace h2
+
+struct h2_group_set {
+    std::vector<h2_matrix*> hs;
+    cudaStream_t stream = nullptr;
+    int lanes = 0, mixed = 0;
+    std::vector<std::vector<h2::LaunchRec>> recs;
+    std::vector<h2::GLaunch> launches;
+    std::vector<void*> dev;
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace h2 {
+
+template <typename Args>
+static int upload_items(h2_group_set* g, const std::vector<const LaunchRec*>& items, Args LaunchRec::*member,
+                        GLaunch& gl) {
+    std::vector<Args> args;
+    std::vector<int> off(1, 0), flag;
+    for (const LaunchRec* r : items) {
+        args.push_back(r->*member);
+        off.push_back(off.back() + (int)r->grid.x);
+        flag.push_back(r->flag);
+    }
+    int rc;
+    Args* da = nullptr;
+    int* doff = nullptr;
+    int* dflag = nullptr;
+    if ((rc = dalloc(&da, args.size())) || (rc = dalloc(&doff, off.size())) || (rc = dalloc(&dflag, flag.size())))
+        return rc;
+    g->dev.push_back(da);
+    g->dev.push_back(doff);
+    g->dev.push_back(dflag);
+    CK(cudaMemcpy(da, args.data(), args.size() * sizeof(Args), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(doff, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dflag, flag.data(), flag.size() * sizeof(int), cudaMemcpyHostToDevice));
+    gl.d_args = da;
+    gl.d_off = doff;
+    gl.d_flag = dflag;
+    gl.n = (int)items.size();
+    gl.gx = (unsigned)off.back();
+    return H2_OK;
+}
+
+static void launch_grouped(const GLaunch& gl, cudaStream_t st) {
+    const dim3 grid(gl.gx, gl.gy);
+    GroupArgs<FactorArgs> F{(const FactorArgs*)gl.d_args, gl.d_off, gl.d_flag, gl.n};
+    GroupArgs<SchurArgs> S{(const SchurArgs*)gl.d_args, gl.d_off, gl.d_flag, gl.n};
+    switch (gl.op) {
+        case OP_INIT_LEAF:
+            k_init_leaf_g<<<grid, NT, 0, st>>>(GroupArgs<InitArgs>{(const InitArgs*)gl.d_args, gl.d_off, gl.d_flag, gl.n});
+            break;
+        case OP_RECOMP: k_recomp_g<<<grid, NT, 0, st>>>(F); break;
+        case OP_RECOMP_CL: k_recomp_cluster_g<<<grid, NT, gl.smem, st>>>(F); break;
+        case OP_ROTATE:
+            if (gl.variant == 0) k_rotate_fp64_g<<<grid, NT, gl.smem, st>>>(F);
+            else if (gl.variant == 8) k_rotate_g<float, 8><<<grid, NT, gl.smem, st>>>(F);
+            else if (gl.variant == 16) k_rotate_g<float, 16><<<grid, NT, gl.smem, st>>>(F);
+            else k_rotate_g<float, 32><<<grid, NT, gl.smem, st>>>(F);
+            break;
+        case OP_LDL:
+            if (gl.variant == 128) k_ldl_g<128><<<grid, 128, gl.smem, st>>>(F);
+            else k_ldl_g<NT><<<grid, NT, gl.smem, st>>>(F);
+            break;
+        case OP_TRSM:
+            if (gl.variant) k_trsm_g<float><<<grid, NT, gl.smem, st>>>(F);
+            else k_trsm_g<double><<<grid, NT, gl.smem, st>>>(F);
+            break;
+        case OP_SCHUR:
+            if (gl.variant == 1) k_schur_f32_g<<<grid, NT, 0, st>>>(S);
+            else if (gl.variant == 2) k_schur_oz_g<<<grid, NT, 0, st>>>(S);
+            else k_schur_g<double><<<grid, NT, 0, st>>>(S);
+            break;
+        case OP_MERGE:
+            k_merge_g<<<grid, NT, 0, st>>>(GroupArgs<MergeArgs>{(const MergeArgs*)gl.d_args, gl.d_off, gl.d_flag, gl.n});
+            break;
+        default:
+            for (const LaunchRec* r : gl.tiny) r->tiny(st);
+            break;
+    }
+}
+
+void group_destroy(h2_group_set* g) {
+    if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    for (void* p : g->dev) cudaFree(p);
+    delete g;
+}
+
+int group_create(h2_matrix* const* hs, int nh, h2_group_set** out) {
+    auto* g = new h2_group_set();
+    g->hs.assign(hs, hs + nh);
+    g->stream = hs[0]->stream;
+    g->lanes = hs[0]->ws.lanes;
+    g->mixed = hs[0]->opt.precision == H2_PREC_MIXED ? 1 : 0;
+    for (h2_matrix* h : g->hs)
+        if (h->ws.lanes != g->lanes || h->opt.precision != hs[0]->opt.precision) {
+            delete g;
+            set_error("h2_group_create: handles need equal max_lanes and precision");
+            return H2_ERR_INVALID_ARG;
+        }
+    CK(cudaFuncSetAttribute(k_rotate_fp64_g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_rotate_g<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_rotate_g<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_rotate_g<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_ldl_g<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_ldl_g<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_trsm_g<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_trsm_g<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    // records of every handle, ordered by (phase, step, colour, op, variant)
+    struct Ref {
+        const LaunchRec* r;
+        int h;
+    };
+    std::vector<Ref> all;
+    g->recs.resize(nh);
+    for (int i = 0; i < nh; ++i) g->recs[i] = factor_records(g->hs[i], g->mixed);
+    for (int i = 0; i < nh; ++i)
+        for (const LaunchRec& r : g->recs[i]) all.push_back(Ref{&r, i});
+    auto key = [](const LaunchRec* r) {
+        return std::make_tuple(r->phase, r->step, r->colour, r->op, r->variant);
+    };
+    std::stable_sort(all.begin(), all.end(), [&](const Ref& a, const Ref& b) { return key(a.r) < key(b.r); });
+    int rc;
+    for (size_t i = 0; i < all.size();) {
+        size_t j = i;
+        std::vector<const LaunchRec*> items;
+        while (j < all.size() && key(all[j].r) == key(all[i].r)) items.push_back(all[j++].r);
+        const LaunchRec* r0 = items[0];
+        GLaunch gl;
+        gl.op = r0->op;
+        gl.variant = r0->variant;
+        gl.block = r0->block;
+        gl.gy = r0->grid.y;
+        for (const LaunchRec* r : items) gl.smem = std::max(gl.smem, r->smem);
+        rc = H2_OK;
+        switch (r0->op) {
+            case OP_INIT_LEAF: rc = upload_items(g, items, &LaunchRec::ia, gl); break;
+            case OP_SCHUR: rc = upload_items(g, items, &LaunchRec::sa, gl); break;
+            case OP_MERGE: rc = upload_items(g, items, &LaunchRec::ma, gl); break;
+            case OP_RECOMP: case OP_RECOMP_CL: case OP_ROTATE: case OP_LDL: case OP_TRSM:
+                rc = upload_items(g, items, &LaunchRec::fa, gl);
+                break;
+            default: gl.tiny = items; break;
+        }
+        if (rc) {
+            group_destroy(g);
+            return rc;
+        }
+        g->launches.push_back(gl);
+        i = j;
+    }
+    // one graph for the whole group batch
+    cudaStream_t st = g->stream;
+    cudaGraph_t graph;
+    CK(cudaStreamSynchronize(st));
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    for (const GLaunch& gl : g->launches) launch_grouped(gl, st);
+    CK(cudaStreamEndCapture(st, &graph));
+    CK(cudaGraphInstantiate(&g->graph, graph, 0));
+    cudaGraphDestroy(graph);
+    *out = g;
+    return H2_OK;
+}
+
+int group_launches(const h2_group_set* g) {
+    int n = 0;
+    for (const GLaunch& gl : g->launches) n += gl.tiny.empty() ? 1 : (int)gl.tiny.size();
+    return n;
+}
+
+int group_inertia(h2_group_set* g, const double* d_shifts, const int* ns, int64_t* d_counts, double* d_minpiv) {
+    const int nh = (int)g->hs.size(), LN = g->lanes;
+    cudaStream_t st = g->stream;
+    for (int i = 0; i < nh; ++i)
+        if (ns[i] < 0 || ns[i] > LN) {
+            set_error("h2_group_inertia_device: ns outside 0..max_lanes");
+            return H2_ERR_INVALID_ARG;
+        }
+    for (int i = 0; i < nh; ++i) {
+        h2_matrix* h = g->hs[i];
+        if (ns[i] > 0)
+            CK(cudaMemcpyAsync(h->ws.d_shifts, d_shifts + (size_t)i * LN, ns[i] * sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
+        k_set_int<<<1, 1, 0, st>>>(state_of(h)->d_active, ns[i]);
+    }
+    CK(cudaGraphLaunch(g->graph, st));
+    for (int i = 0; i < nh; ++i) {
+        if (ns[i] == 0) continue;
+        FactorState* fs = state_of(g->hs[i]);
+        CK(cudaMemcpyAsync(d_counts + (size_t)i * LN, fs->d_counts, ns[i] * sizeof(int64_t),
+                           cudaMemcpyDeviceToDevice, st));
+        if (d_minpiv)
+            CK(cudaMemcpyAsync(d_minpiv + (size_t)i * LN, fs->d_mp, ns[i] * sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaGetLastError());
+    return H2_OK;
 }
 
 static int ensure_graph(h2_matrix* h, int mixed) {

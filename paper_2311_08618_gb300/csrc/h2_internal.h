@@ -159,6 +159,10 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
             double* err_bound);
 void free_workspace(h2_matrix* h);
 int run_status(h2_matrix* h, int64_t* info);
+int group_create(h2_matrix* const* hs, int nh, h2_group_set** out);
+int group_inertia(h2_group_set* g, const double* d_shifts, const int* ns, int64_t* d_counts, double* d_minpiv);
+int group_launches(const h2_group_set* g);
+void group_destroy(h2_group_set* g);
 void heartbeat_read(unsigned int* out);
 void free_device(h2_matrix* h);
 }  // namespace h2
