@@ -499,6 +499,7 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
              "batched_fp64_over_plain": value / plain_rate,
              "batched_mixed_over_plain": precision["value"] / plain_rate}
     serving_res = _serving(args) if args.serving_s > 0 and world == 1 else None
+    batching_res = _batching(args) if args.batch_count > 0 and world == 1 else None
     ws_mb = info["workspace_bytes"] / 1e6
     line = {"metric": METRIC, "value": value, "unit": "shifts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -516,7 +517,7 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
                      "rounds": info2["last_rounds"], "shifts_per_solve": info2["last_shifts"],
                      "lambda": lam[0], "err_bound": lam[1]},
             "build_s": build_s, "roofline": roof, "clocks": clocks, "precision": precision,
-            "fp64_tc": fp64_tc, "plain_fp64": plain, "serving": serving_res}
+            "fp64_tc": fp64_tc, "plain_fp64": plain, "serving": serving_res, "batching": batching_res}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         sample = list(sh[args.warmup][:: max(1, lanes // (2 * cores))][:2 * cores])
@@ -533,6 +534,67 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
 
 
 SERVING_SIZES = (1024, 2048, 4096, 8192)
+
+
+def _tune_summary(mats):
+    """(levels with one warp per Bunch-Kaufman block, levels with a clustered
+    recompression) / levels, over all handles."""
+    n = t128 = clu = 0
+    for M in mats:
+        for l in range(M.h2_info()["levels"]):
+            t, c = M.h2_autotune_choice(l)
+            n += 1
+            t128 += t == 32
+            clu += c
+    return "%d/%d, %d/%d" % (t128, n, clu, n)
+
+
+def _batching(args):
+    """The many-matrix configuration on a bounded sample: the first
+    --batch-count members of the seeded 512-matrix list (workloads.batch_members)
+    with n <= --batch-nmax, FP64, --batch-lanes lanes each, their own random k,
+    tol 1e-8.  All k-th eigenvalues through group batches (one launch per tree
+    level and colour over all matrices), against the same handles solved one
+    after another with h2_kth_eig."""
+    import torch
+    import paper_2311_08618_gb300 as pkg
+    from paper_2311_08618_gb300 import batching
+    members = [w for w in W.batch_members(512) if w.points.shape[0] <= args.batch_nmax][:args.batch_count]
+    st = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    mats = [pkg.H2Matrix(w.points, w.kernel, w.kparams, leaf=w.leaf, rank=w.rank, eta=w.eta,
+                         max_lanes=args.batch_lanes, stream=st.cuda_stream, autotune=1) for w in members]
+    G = pkg.H2Group(mats)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    ks = [w.ks[0] for w in members]
+    tol = 1e-8
+    batching.kth_group(mats, ks, 1e3, st, G)          # warm-up rounds
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam_g, rounds, shifts = batching.kth_group(mats, ks, tol, st, G)
+    tg = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam_s = np.array([M.h2_kth_eig([k], tol)[0][0] for M, k in zip(mats, ks)])
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    ns = [w.points.shape[0] for w in members]
+    res = {"sample": "first %d of the 512-matrix list with n <= %d (n %d..%d, %d in 3D); FP64, %d lanes each"
+                     % (len(members), args.batch_nmax, min(ns), max(ns),
+                        sum(w.points.shape[1] == 3 for w in members), args.batch_lanes),
+           "eigs_per_s": len(members) / tg, "sequential_eigs_per_s": len(members) / ts,
+           "speedup_vs_sequential": ts / tg, "rounds": rounds, "shifts": shifts,
+           "launches_per_group_batch": G.launches(),
+           "launches_per_sequential_round": int(sum(M.h2_info()["kernels_per_batch"] for M in mats)),
+           "max_abs_diff_vs_sequential": float(np.max(np.abs(lam_g - lam_s))), "tol": tol,
+           "build_s": build_s, "autotune": "per level: Bunch-Kaufman on one warp or one CTA per block, "
+                                            "recompression on one CTA or an 8-CTA cluster, timed at build; "
+                                            "levels choosing (warp, clustered): %s" % _tune_summary(mats)}
+    G.close()
+    for M in mats:
+        M.close()
+    return res
 
 
 def _serving_run(args, rate, seconds, seed):
@@ -596,6 +658,9 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=40.0)
     ap.add_argument("--serving-sustain-rate", type=float, default=2.0, help="second, sustainable rate (0: skip)")
     ap.add_argument("--serving-sustain-s", type=float, default=5.0)
+    ap.add_argument("--batch-count", type=int, default=24, help="matrices of the batching sample (0: skip)")
+    ap.add_argument("--batch-nmax", type=int, default=8192)
+    ap.add_argument("--batch-lanes", type=int, default=4)
     ap.add_argument("--serving-lanes", type=int, default=16)
     ap.add_argument("--workload", default="laplace2d_n1024", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1], help="0 FP64, 1 mixed (main handle)")

@@ -20,7 +20,8 @@ H2_PREC_FP64, H2_PREC_MIXED, H2_PREC_FP64_TC = 0, 1, 2
 EXPORTED_SYMBOLS = ["h2_default_options", "h2_build", "h2_destroy", "h2_last_error", "h2_inertia",
                     "h2_inertia_device", "h2_kth_eig", "h2_info", "h2_tree_perm", "h2_level_ranks",
                     "h2_profile_batch", "h2_dense_inertia_noalloc", "h2_status", "h2_heartbeat",
-                    "h2_group_create", "h2_group_inertia_device", "h2_group_launches", "h2_group_destroy"]
+                    "h2_group_create", "h2_group_inertia_device", "h2_group_launches", "h2_group_destroy",
+                    "h2_autotune_choice"]
 KIND_NAMES = ["init", "recomp", "rotate", "ldl", "trsm", "schur", "merge", "other"]
 
 
@@ -32,7 +33,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("admissibility", C.c_int), ("eps_h2", C.c_double),
                 ("fill_cap", C.c_int), ("sketch_cols", C.c_int), ("seed", C.c_uint64),
                 ("max_lanes", C.c_int), ("pivot_guard", C.c_double), ("stream", C.c_void_p),
-                ("graphs", C.c_int), ("recomp_cluster_cols", C.c_int)]
+                ("graphs", C.c_int), ("recomp_cluster_cols", C.c_int), ("autotune", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -94,6 +95,8 @@ def lib():
         L.h2_group_launches.restype = C.c_int
         L.h2_group_destroy.argtypes = [P]
         L.h2_group_destroy.restype = None
+        L.h2_autotune_choice.argtypes = [P, C.c_int, P]
+        L.h2_autotune_choice.restype = C.c_int
         for f in ("h2_build", "h2_inertia", "h2_inertia_device", "h2_kth_eig", "h2_info",
                   "h2_tree_perm", "h2_level_ranks", "h2_profile_batch"):
             getattr(L, f).restype = C.c_int
@@ -198,6 +201,12 @@ class H2Matrix:
         p = np.zeros(self.n, dtype=np.int64)
         _check(lib().h2_tree_perm(self._h, p.ctypes.data_as(C.c_void_p)))
         return p
+
+    def h2_autotune_choice(self, level):
+        """(threads per Bunch-Kaufman CTA, 1 if the recompression is clustered) of a level."""
+        out = np.zeros(2, dtype=np.int32)
+        _check(lib().h2_autotune_choice(self._h, int(level), out.ctypes.data_as(C.c_void_p)))
+        return int(out[0]), int(out[1])
 
     def h2_level_ranks(self, level):
         r = np.zeros(1 << level, dtype=np.int32)

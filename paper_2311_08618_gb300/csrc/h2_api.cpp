@@ -138,6 +138,12 @@ int h2_inertia_device(h2_handle h, const double* d_shifts, int64_t ns, int64_t* 
     return run_inertia(h, d_shifts, (int)ns, d_counts, d_min_abs_pivot);
 }
 
+int h2_autotune_choice(h2_handle h, int level, int* out) {
+    g_last_error.clear();
+    if (!h || !out || level < 0 || level > h->plan.L) { set_error("h2_autotune_choice: bad arguments"); return H2_ERR_INVALID_ARG; }
+    return tune_choice(h, level, out);
+}
+
 int h2_group_create(const h2_handle* hs, int nh, h2_group* out) {
     g_last_error.clear();
     if (!hs || !out || nh < 1) { set_error("h2_group_create: bad arguments"); return H2_ERR_INVALID_ARG; }

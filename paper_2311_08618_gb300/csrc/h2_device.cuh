@@ -432,6 +432,173 @@ __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, doubl
     __syncthreads();
 }
 
+// The same Bunch-Kaufman LDL^T as cta_bk_ldl, run by one warp: the same
+// pivot search (largest |value|, first index on ties), the same decisions and
+// the same expression for every updated element, with warp shuffles for the
+// reductions and __syncwarp for the barriers.  The trailing update walks the
+// (row, column) pairs of the trailing block as one flat index, so no lane
+// idles on a partial row.  neg / minpiv / bad are lane 0's accumulators.
+__device__ __forceinline__ void warp_argmax(double& v, int& idx) {
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+}
+
+__device__ inline void warp_bk_ldl(double* S, int lds, int n, int* perm, int* piv, int* neg, double* minpiv, int* bad,
+                            double zero_pivot, double* buf) {
+    const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+    const int lane = threadIdx.x & 31;
+    double* c0 = buf;
+    double* c1 = buf + n;
+    double* l0 = buf + 2 * n;
+    double* l1 = buf + 3 * n;
+    for (int i = lane; i < n; i += 32) perm[i] = i;
+    __syncwarp();
+    int k = 0, nneg = 0;
+    double mp = 1.0 / 0.0;
+    while (k < n) {
+        double akk = fabs(S[(size_t)k * lds + k]);
+        double lam = -1.0;
+        int r = 0x7fffffff;
+        for (int i = k + 1 + lane; i < n; i += 32) {
+            double v = fabs(S[(size_t)i * lds + k]);
+            if (v > lam) { lam = v; r = i; }
+        }
+        warp_argmax(lam, r);
+        if (k + 1 >= n) { lam = 0.0; r = k; }
+        else if (r <= k || r >= n) r = k + 1;
+        int size = 1;
+        int swap_a = -1, swap_b = -1;
+        if (!(akk == akk) || !(lam == lam)) {
+            if (lane == 0) *bad = 1;
+        } else if (!(lam == 0.0 || akk >= alpha * lam)) {
+            double sig = -1.0;
+            int bj = 0x7fffffff;
+            for (int j = k + lane; j < n; j += 32) {
+                if (j == r) continue;
+                double v = fabs(S[(size_t)j * lds + r]);
+                if (v > sig) { sig = v; bj = j; }
+            }
+            warp_argmax(sig, bj);
+            if (sig < 0.0) sig = 0.0;
+            if (akk * sig >= alpha * lam * lam) {
+                // 1x1 at k
+            } else if (fabs(S[(size_t)r * lds + r]) >= alpha * sig) {
+                swap_a = k; swap_b = r;
+            } else {
+                swap_a = k + 1; swap_b = r;
+                size = 2;
+            }
+        }
+        if (swap_a >= 0 && swap_a != swap_b) {
+            __syncwarp();
+            for (int j = lane; j < n; j += 32) {
+                double t = S[(size_t)swap_a * lds + j];
+                S[(size_t)swap_a * lds + j] = S[(size_t)swap_b * lds + j];
+                S[(size_t)swap_b * lds + j] = t;
+            }
+            __syncwarp();
+            for (int i = lane; i < n; i += 32) {
+                double t = S[(size_t)i * lds + swap_a];
+                S[(size_t)i * lds + swap_a] = S[(size_t)i * lds + swap_b];
+                S[(size_t)i * lds + swap_b] = t;
+            }
+            if (lane == 0) {
+                int t = perm[swap_a];
+                perm[swap_a] = perm[swap_b];
+                perm[swap_b] = t;
+            }
+        }
+        __syncwarp();
+        if (size == 1) {
+            double d = S[(size_t)k * lds + k];
+            if (d == 0.0 && zero_pivot != 0.0) d = zero_pivot;
+            __syncwarp();
+            if (lane == 0) {
+                S[(size_t)k * lds + k] = d;
+                piv[k] = 1;
+                if (d < 0.0) nneg += 1;
+                mp = fmin(mp, fabs(d));
+                if (d != d) *bad = 1;
+            }
+            const int t = n - k - 1;
+            if (d != 0.0 && t > 0) {
+                const double invd = 1.0 / d;
+                for (int i = k + 1 + lane; i < n; i += 32) {
+                    double c = S[(size_t)i * lds + k];
+                    c0[i] = c;
+                    l0[i] = c * invd;
+                }
+                __syncwarp();
+                {   // flat (row, column) walk, stepping 32 = di rows + dj columns
+                    const int di = 32 / t, dj = 32 % t;
+                    int i = lane / t, j = lane % t;
+                    for (int e = lane; e < t * t; e += 32) {
+                        S[(size_t)(k + 1 + i) * lds + k + 1 + j] -= l0[k + 1 + i] * c0[k + 1 + j];
+                        i += di;
+                        j += dj;
+                        if (j >= t) { j -= t; ++i; }
+                    }
+                }
+                for (int i = k + 1 + lane; i < n; i += 32) S[(size_t)i * lds + k] = l0[i];
+            }
+            __syncwarp();
+            k += 1;
+        } else {
+            double a = S[(size_t)k * lds + k], b = S[(size_t)(k + 1) * lds + k],
+                   c = S[(size_t)(k + 1) * lds + k + 1];
+            double det = a * c - b * b;
+            if (lane == 0) {
+                piv[k] = 2;
+                piv[k + 1] = 0;
+                double tr = a + c;
+                nneg += det < 0.0 ? 1 : (tr < 0.0 ? 2 : 0);
+                double disc = sqrt(fmax(0.0, 0.25 * (a - c) * (a - c) + b * b));
+                double e0 = 0.5 * tr - disc, e1 = 0.5 * tr + disc;
+                mp = fmin(mp, fmin(fabs(e0), fabs(e1)));
+                if (det != det) *bad = 1;
+            }
+            const int t = n - k - 2;
+            if (t > 0) {
+                const double idet = 1.0 / det;
+                double i00 = c * idet, i01 = -b * idet, i11 = a * idet;
+                for (int i = k + 2 + lane; i < n; i += 32) {
+                    double ci0 = S[(size_t)i * lds + k], ci1 = S[(size_t)i * lds + k + 1];
+                    c0[i] = ci0;
+                    c1[i] = ci1;
+                    l0[i] = ci0 * i00 + ci1 * i01;
+                    l1[i] = ci0 * i01 + ci1 * i11;
+                }
+                __syncwarp();
+                {
+                    const int di = 32 / t, dj = 32 % t;
+                    int i = lane / t, j = lane % t;
+                    for (int e = lane; e < t * t; e += 32) {
+                        const int ii = k + 2 + i, jj = k + 2 + j;
+                        S[(size_t)ii * lds + jj] -= l0[ii] * c0[jj] + l1[ii] * c1[jj];
+                        i += di;
+                        j += dj;
+                        if (j >= t) { j -= t; ++i; }
+                    }
+                }
+                for (int i = k + 2 + lane; i < n; i += 32) {
+                    S[(size_t)i * lds + k] = l0[i];
+                    S[(size_t)i * lds + k + 1] = l1[i];
+                }
+            }
+            __syncwarp();
+            k += 2;
+        }
+    }
+    if (lane == 0) {
+        *neg += nneg;
+        *minpiv = fmin(*minpiv, mp);
+    }
+    __syncwarp();
+}
+
 // L(j, i) of the unit lower factor stored by cta_bk_ldl (i < j).
 __device__ __forceinline__ double bk_L(const double* S, int lds, const int* piv, int j, int i) {
     if (piv[i] == 2 && j == i + 1) return 0.0;

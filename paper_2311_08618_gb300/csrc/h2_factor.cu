@@ -155,6 +155,7 @@ struct FactorArgs {
     int* err;
     const int* active;
     double* stats;   // [2 * H2_NKINDS]: algorithmic flops, then bytes, per kernel kind
+    int ncl;         // clusters of this colour
 };
 
 __device__ __forceinline__ double* slot_ptr(double* slots, int s, int lanes, int lane, int D) {
@@ -818,6 +819,69 @@ template <int NTH>
 __global__ void __launch_bounds__(NTH) k_ldl_g(GroupArgs<FactorArgs> G) {
     const int m = group_find(G.off, G.n, blockIdx.x);
     k_ldl_body<NTH>(G.args[m], G.flag[m], blockIdx.x - G.off[m], blockIdx.y);
+}
+
+// The same step with one warp per (cluster, lane) block, LW blocks per CTA
+// (blocks of dimension <= 64): warp w of CTA bx takes item bx * LW + w of the
+// colour's ncl * lanes items, its block staged in its own shared-memory slice.
+constexpr int LW = 2;
+__host__ __device__ constexpr size_t ldl_warp_slice(int D) { return (size_t)D * D + 4 * (size_t)D; }
+__device__ __forceinline__ void k_ldl_warp_body(const FactorArgs& A, const int bx) {
+    HbScope hb_(3);
+    const int w = threadIdx.x / 32, l32 = threadIdx.x % 32;
+    const int LN = A.lanes, D = A.D;
+    const int item = bx * LW + w;
+    if (item >= A.ncl * LN) return;
+    const int ci = item % A.ncl, lane = item / A.ncl;
+    if (lane >= *A.active) return;
+    extern __shared__ double sW[];
+    double* S = sW + (size_t)w * ldl_warp_slice(D);
+    const int p = A.cl[ci];
+    const int m = A.dim[p * LN + lane], rk1 = A.rk[p * LN + lane];
+    const int Rp = m - rk1;
+    double* scr = A.scratch + ((size_t)ci * LN + lane) * A.lay.total;
+    int* hdr = (int*)(scr + A.lay.hdr);
+    if (m < 0 || m > D || rk1 < 0 || rk1 > m) {
+        if (l32 == 0) {
+            hdr[0] = 0;
+            hdr[1] = 0;
+            report_bad(A.err, 3, m, rk1, D, 0);
+        }
+        return;
+    }
+    if (l32 == 0) {
+        hdr[0] = rk1;
+        hdr[1] = Rp;
+    }
+    if (Rp <= 0) return;
+    double* F = scr + A.lay.f;
+    int* perm = (int*)(scr + A.lay.iperm);
+    int* piv = perm + D;
+    const double* Bpp = slot_ptr(A.slots, A.targ_slot[ci * A.ntarg_max], LN, lane, D);   // target 0 = p
+    for (int e = l32; e < Rp * Rp; e += 32) {
+        int i = e / Rp, j = e % Rp;
+        S[(size_t)i * Rp + j] = Bpp[(size_t)(rk1 + i) * D + rk1 + j];
+    }
+    __syncwarp();
+    int neg = 0, bad = 0;
+    double mp = 1.0 / 0.0;
+    warp_bk_ldl(S, Rp, Rp, perm, piv, &neg, &mp, &bad, A.zero_pivot, S + (size_t)Rp * Rp);
+    for (int e = l32; e < Rp * Rp; e += 32) {
+        int i = e / Rp, j = e % Rp;
+        F[(size_t)i * D + j] = S[(size_t)i * Rp + j];
+    }
+    if (l32 == 0) {
+        atomicAdd(&A.neg[lane], (unsigned long long)neg);
+        if (!(mp >= 0.0)) mp = 0.0;
+        atomicMin(&A.minpiv[lane], (unsigned long long)__double_as_longlong(mp));
+        if (bad) atomicOr(A.err, 1);
+        add_stats(A.stats, H2_KIND_LDL, (double)Rp * Rp * Rp / 3.0, 16.0 * (double)Rp * Rp);
+    }
+}
+__global__ void __launch_bounds__(32 * LW) k_ldl_warp(FactorArgs A) { k_ldl_warp_body(A, blockIdx.x); }
+__global__ void __launch_bounds__(32 * LW) k_ldl_warp_g(GroupArgs<FactorArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_ldl_warp_body(G.args[m], blockIdx.x - G.off[m]);
 }
 
 // Digits of the FP64_TC Schur products (see k_schur_oz).
@@ -1542,6 +1606,7 @@ static FactorState* state_of(h2_matrix* h) {
 }
 
 static int ensure_graph(h2_matrix* h, int mixed);
+static int autotune(h2_matrix* h);
 // graphs unless the handle asks for plain launches or the environment
 // variable H2_NO_GRAPH=1 (a diagnostic) turns them off for the process
 static bool use_graphs(const h2_matrix* h) {
@@ -1672,6 +1737,7 @@ int alloc_workspace(h2_matrix* h, int lanes) {
     CK(cudaFuncSetAttribute(k_rotate<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     CK(cudaFuncSetAttribute(k_ldl<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
     CK(cudaFuncSetAttribute(k_ldl<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_ldl_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     CK(cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
     CK(cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
     // buffers
@@ -1700,6 +1766,7 @@ int alloc_workspace(h2_matrix* h, int lanes) {
     // capture the batch graphs now, while nothing else runs on the device:
     // a capture never overlaps other handles' work on other streams
     CK(cudaStreamSynchronize(h->stream));
+    if (h->opt.autotune && (rc = autotune(h))) return rc;
     if (use_graphs(h)) {
         if ((rc = ensure_graph(h, 0))) return rc;
         if (h->opt.precision == H2_PREC_MIXED && (rc = ensure_graph(h, 1))) return rc;
@@ -1754,6 +1821,18 @@ struct LaunchRec {
     std::function<void(cudaStream_t)> tiny;
 };
 
+// kernel choices of a level: autotuned when the handle has them, else the
+// fixed rules (128 threads for blocks up to 64, clusters for wide Z)
+static int ldl_threads(const h2_matrix* h, int l, int Dm) {
+    if (l < (int)h->tune_ldl.size() && h->tune_ldl[l] > 0) return (h->tune_ldl[l] == 32 && Dm > 64) ? NT : h->tune_ldl[l];
+    return Dm <= 64 ? 32 : NT;
+}
+static bool recomp_clustered(const h2_matrix* h, int l, int nfill_max, int Dm) {
+    if (l < (int)h->tune_recomp.size() && h->tune_recomp[l] >= 0) return h->tune_recomp[l] == 1;
+    const int wide = h->opt.recomp_cluster_cols;
+    return wide >= 0 && (size_t)nfill_max * Dm >= (wide > 0 ? (size_t)wide : kWideFill);
+}
+
 static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
     std::vector<LaunchRec> R;
     const Plan& P = h->plan;
@@ -1801,16 +1880,16 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
                           C.rowblk_trans, C.rowblk_fill, C.nrow, C.nrow_max, C.fillq, C.fillslot, C.nfill,
                           C.nfill_max, ws.d_scratch, W.lay, h->tol, 2.220446049250313e-16 * h->norm_inf,
                           h->fill_cap_eff, ws.d_neg, ws.d_minpiv, ws.d_err, fs->d_active, fs->d_stats};
+            fa.ncl = C.ncl;
             LaunchRec r;
             r.phase = 2;
             r.step = L - l;
             r.colour = c;
             r.fa = fa;
             if (C.has_fill) {
-                const int wide = h->opt.recomp_cluster_cols;
                 LaunchRec q = r;
                 q.kind = H2_KIND_RECOMP;
-                if (wide >= 0 && (size_t)C.nfill_max * Dm >= (wide > 0 ? (size_t)wide : kWideFill)) {
+                if (recomp_clustered(h, l, C.nfill_max, Dm)) {
                     q.op = OP_RECOMP_CL;
                     q.grid = dim3(C.ncl * QG, LN);
                     q.smem = (size_t)Dm * sizeof(double);
@@ -1838,10 +1917,17 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
                 q.op = OP_LDL;
                 q.kind = H2_KIND_LDL;
                 q.flag = sm_ldl <= kSmemCap ? 1 : 0;
-                q.variant = Dm <= 64 ? 128 : NT;
-                q.block = q.variant;
-                q.smem = q.flag ? sm_ldl : 0;
-                q.grid = dim3(C.ncl, LN);
+                q.variant = ldl_threads(h, l, Dm);
+                if (q.variant == 32) {           // one warp per block
+                    q.block = 32 * LW;
+                    q.flag = 1;
+                    q.smem = LW * ldl_warp_slice(Dm) * sizeof(double);
+                    q.grid = dim3((C.ncl * LN + LW - 1) / LW, 1);
+                } else {
+                    q.block = q.variant;
+                    q.smem = q.flag ? sm_ldl : 0;
+                    q.grid = dim3(C.ncl, LN);
+                }
                 R.push_back(q);
             }
             {
@@ -1926,7 +2012,8 @@ static void launch_single(const LaunchRec& r, cudaStream_t st) {
             else k_rotate<float, 32><<<r.grid, NT, r.smem, st>>>(r.fa);
             break;
         case OP_LDL:
-            if (r.variant == 128) k_ldl<128><<<r.grid, 128, r.smem, st>>>(r.fa, r.flag);
+            if (r.variant == 32) k_ldl_warp<<<r.grid, 32 * LW, r.smem, st>>>(r.fa);
+            else if (r.variant == 128) k_ldl<128><<<r.grid, 128, r.smem, st>>>(r.fa, r.flag);
             else k_ldl<NT><<<r.grid, NT, r.smem, st>>>(r.fa, r.flag);
             break;
         case OP_TRSM:
@@ -1952,6 +2039,69 @@ static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, 
         if (prof) prof->after();
     }
     return nl;
+}
+
+// Autotuning (h2_options.autotune): both candidates of every per-level
+// choice run on full batches of shifts spread over the Gershgorin interval;
+// each launch is timed with CUDA events on the handle's stream (the second of
+// two runs per candidate, warm), and every level keeps its faster kernel.
+static int autotune(h2_matrix* h) {
+    const int L = h->plan.L;
+    Workspace& ws = h->ws;
+    FactorState* fs = state_of(h);
+    cudaStream_t st = h->stream;
+    const int mixed = h->opt.precision == H2_PREC_MIXED ? 1 : 0;
+    const int LN = ws.lanes;
+    std::vector<double> sh(LN);
+    for (int i = 0; i < LN; ++i) sh[i] = h->glo + (h->ghi - h->glo) * (i + 0.5) / LN;
+    CK(cudaMemcpyAsync(ws.d_shifts, sh.data(), LN * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_set_int<<<1, 1, 0, st>>>(fs->d_active, LN);
+    const int cand_ldl[2] = {32, NT}, cand_rc[2] = {0, 1};   // 32: one warp per block (blocks <= 64)
+    std::vector<double> t_ldl[2], t_rc[2];
+    for (int c = 0; c < 2; ++c) {
+        t_ldl[c].assign(L + 1, 0.0);
+        t_rc[c].assign(L + 1, 0.0);
+        h->tune_ldl.assign(L + 1, cand_ldl[c]);
+        h->tune_recomp.assign(L + 1, cand_rc[c]);
+        for (int rep = 0; rep < 2; ++rep) {
+            std::vector<LaunchRec> recs = factor_records(h, mixed);
+            std::vector<cudaEvent_t> ev(2 * recs.size());
+            for (auto& e : ev) CK(cudaEventCreate(&e));
+            for (size_t i = 0; i < recs.size(); ++i) {
+                CK(cudaEventRecord(ev[2 * i], st));
+                launch_single(recs[i], st);
+                CK(cudaEventRecord(ev[2 * i + 1], st));
+            }
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(st));
+            for (size_t i = 0; rep == 1 && i < recs.size(); ++i) {
+                const LaunchRec& r = recs[i];
+                if (r.phase != 2) continue;
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]));
+                const int l = L - r.step;
+                if (r.op == OP_LDL) t_ldl[c][l] += t;
+                if (r.op == OP_RECOMP || r.op == OP_RECOMP_CL) t_rc[c][l] += t;
+            }
+            for (auto& e : ev) cudaEventDestroy(e);
+        }
+    }
+    for (int l = 0; l <= L; ++l) {
+        h->tune_ldl[l] = t_ldl[0][l] <= t_ldl[1][l] ? cand_ldl[0] : cand_ldl[1];
+        h->tune_recomp[l] = t_rc[0][l] <= t_rc[1][l] ? cand_rc[0] : cand_rc[1];
+    }
+    CK(cudaMemsetAsync(ws.d_err, 0, 8 * sizeof(int), st));
+    CK(cudaStreamSynchronize(st));
+    return H2_OK;
+}
+
+int tune_choice(h2_matrix* h, int level, int* out) {
+    const int Dm = h->lev[level].dmax;
+    const LevelWork& W = state_of(h)->lw[level];
+    const int nfm = W.colours.empty() ? 0 : W.colours[0].nfill_max;
+    out[0] = ldl_threads(h, level, Dm);
+    out[1] = recomp_clustered(h, level, nfm, Dm) ? 1 : 0;
+    return H2_OK;
 }
 
 // ------------------------------------------------------------ groups --
@@ -2030,7 +2180,8 @@ static void launch_grouped(const GLaunch& gl, cudaStream_t st) {
             else k_rotate_g<float, 32><<<grid, NT, gl.smem, st>>>(F);
             break;
         case OP_LDL:
-            if (gl.variant == 128) k_ldl_g<128><<<grid, 128, gl.smem, st>>>(F);
+            if (gl.variant == 32) k_ldl_warp_g<<<grid, 32 * LW, gl.smem, st>>>(F);
+            else if (gl.variant == 128) k_ldl_g<128><<<grid, 128, gl.smem, st>>>(F);
             else k_ldl_g<NT><<<grid, NT, gl.smem, st>>>(F);
             break;
         case OP_TRSM:
@@ -2076,6 +2227,7 @@ int group_create(h2_matrix* const* hs, int nh, h2_group_set** out) {
     CK(cudaFuncSetAttribute(k_rotate_g<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     CK(cudaFuncSetAttribute(k_rotate_g<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     CK(cudaFuncSetAttribute(k_ldl_g<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_ldl_warp_g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     CK(cudaFuncSetAttribute(k_ldl_g<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
     CK(cudaFuncSetAttribute(k_trsm_g<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
     CK(cudaFuncSetAttribute(k_trsm_g<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));

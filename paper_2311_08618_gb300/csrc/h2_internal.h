@@ -137,6 +137,9 @@ struct h2_matrix {
     std::vector<double> plan_points;  // host copy of the input points (n x d)
     int mmax = 0;                  // largest leaf
     int fill_cap_eff = 0;          // skeleton cap after recompression
+    // autotuned kernel choices per level (0 / -1: the default rules)
+    std::vector<int> tune_ldl;       // k_ldl threads per CTA (128 or 256)
+    std::vector<int> tune_recomp;    // 1: clustered recompression, 0: one CTA
     int last_rounds = 0;           // bisection rounds of the last h2_kth_eig
     int64_t last_shifts = 0;       // shifts evaluated by the last h2_kth_eig
     int kernels_per_batch = 0;     // launches in one batch (graph nodes)
@@ -159,6 +162,7 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
             double* err_bound);
 void free_workspace(h2_matrix* h);
 int run_status(h2_matrix* h, int64_t* info);
+int tune_choice(h2_matrix* h, int level, int* out);
 int group_create(h2_matrix* const* hs, int nh, h2_group_set** out);
 int group_inertia(h2_group_set* g, const double* d_shifts, const int* ns, int64_t* d_counts, double* d_minpiv);
 int group_launches(const h2_group_set* g);

@@ -134,3 +134,27 @@ def test_group_rejects_unequal_lanes(pkg):
     with pytest.raises(pkg.H2Error) as e:
         pkg.H2Group([a, b])
     assert e.value.code == -1
+
+
+def test_group_kth_driver_against_dense(pkg):
+    """batching.kth_group: every matrix's own k to tol 1e-8 in shared group
+    rounds; within tol of the handle's own h2_kth_eig.  Against the dense
+    oracle's eigenvalue the bound is tol + 1e-7 ||A||_inf: these members' rank
+    caps (16) leave compression errors above 1e-8 ||A||, and by Weyl's
+    inequality an eigenvalue moves by at most ||A - A~||_2."""
+    import torch
+    from paper_2311_08618_gb300 import batching
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        mats, pts = _build(pkg, st, 8, 0)
+        ks = [1, 512, 400, 200, 1500]
+        lam, rounds, shifts = batching.kth_group(mats, ks, 1e-8, st)
+        assert rounds > 0 and shifts > 0
+        for i, (M, (X, kind, kp, leaf, rank)) in enumerate(zip(mats, pts)):
+            own, eb = M.h2_kth_eig([ks[i]], 1e-8)
+            assert abs(lam[i] - own[0]) <= 1e-8, i
+            A = dense.kernel_matrix(kind, kp, X)
+            ev = dense.eigenvalues(A)
+            assert abs(lam[i] - ev[ks[i] - 1]) <= 1e-8 + 1e-7 * np.abs(A).sum(axis=1).max(), i
+        for M in mats:
+            M.close()

@@ -86,3 +86,27 @@ def test_clustered_and_single_cta_paths_agree(pkg):
         assert abs(l1 - l2) <= 1e-8
     # lambda_512 of the dense matrix (golden file): within tol + 1e-8 ||A||_2
     assert abs(out[(pkg.H2_PREC_FP64, 1)][2] - 965.7169369317037) <= 1e-8 + 1e-8 * 4109.95
+
+
+def test_autotuned_handle(pkg):
+    """autotune=1: every level reports a valid choice, and the tuned handle's
+    counts equal the dense oracle's at midpoints between eigenvalues (FP64 and
+    mixed)."""
+    X = W.uniform_cube(800, 3, 22)
+    kp = (1e-3, 0, 0, 0)
+    A = dense.kernel_matrix(W.YUKAWA_EPS, kp, X)
+    ev = dense.eigenvalues(A)
+    s = shifts_between(ev, 15)
+    gap = np.abs(s[:, None] - ev[None, :]).min(axis=1)
+    sure = gap > 1e-6 * np.abs(ev).max()
+    want = np.array([np.sum(ev < x) for x in s])
+    for prec in (pkg.H2_PREC_FP64, pkg.H2_PREC_MIXED):
+        M = pkg.H2Matrix(X, W.YUKAWA_EPS, kp, leaf=32, rank=16, max_lanes=16, precision=prec, autotune=1)
+        L = M.h2_info()["levels"] - 1
+        for l in range(L + 1):
+            t, c = M.h2_autotune_choice(l)
+            assert t in (32, 256) and c in (0, 1)
+        got, mp = M.h2_inertia(s)
+        assert np.array_equal(got[sure], want[sure])
+        assert M.h2_status()[0] == 0
+        M.close()

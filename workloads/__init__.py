@@ -114,3 +114,21 @@ def cp_cylinder(seed: int = 4, n: int = 262144) -> Workload:
     32 interior k around n/2."""
     return Workload("cylinder_n%d" % n, cylinder_lattice(n, seed), GAUSS_PLUS_INV,
                     (1e-2, 0.1, 0, 0), 256, 48, 1.0, list(range(n // 2 - 16, n // 2 + 16)), 1e-8)
+
+
+def batch_members(count: int = 512, seed: int = 3) -> list:
+    """The many-matrix configuration: ``count`` independent problems with
+    n = floor(2048 * 16^U) (log-uniform in [2048, 32768]), dimension 2 or 3
+    with probability 1/2, points uniform in the unit square or cube (point
+    seed 1000 * seed + i), kernel 1/(r + 1e-3), leaf/rank 64/16 in 2D and
+    256/32 in 3D, and k uniform in 1..n.  Returns Workload descriptions."""
+    u = uniform(seed, 3 * count)
+    out = []
+    for i in range(count):
+        n = int(2048.0 * 16.0 ** u[3 * i])
+        d = 2 if u[3 * i + 1] < 0.5 else 3
+        k = 1 + int(u[3 * i + 2] * n)
+        leaf, rank = (64, 16) if d == 2 else (256, 32)
+        out.append(Workload("batch%d_d%d_n%d" % (i, d, n), uniform_cube(n, d, 1000 * seed + i), LAPLACE_EPS,
+                            (1e-3, 0, 0, 0), leaf, rank, 1.0, [k], 1e-8))
+    return out
