@@ -19,6 +19,34 @@ import numpy as np
 from .binding import H2Group
 
 
+def bracket_rounds(a, b, ks, tol, lanes, evaluate):
+    """The host side of the rounds: brackets [a_i, b_i] of lambda_{k_i},
+    narrowed until b_i - a_i < tol.  evaluate(mu, ns) returns the counts
+    nu(mu[i, j]) for j < ns[i] (mu: matrices x lanes array, ns: shifts per
+    matrix, 0 for finished ones).  Returns (midpoints, rounds, shifts)."""
+    a = np.array(a, dtype=np.float64)
+    b = np.array(b, dtype=np.float64)
+    k = np.asarray(ks, dtype=np.int64)
+    frac = np.arange(1, lanes + 1) / (lanes + 1.0)
+    rounds = shifts = 0
+    while True:
+        act = (b - a) >= tol
+        if not act.any():
+            break
+        mu = a[:, None] + (b - a)[:, None] * frac[None, :]
+        ns = np.where(act, lanes, 0)
+        nu = evaluate(mu, ns)
+        for i in np.nonzero(act)[0]:
+            hi_side = nu[i] >= k[i]
+            if hi_side.any():
+                b[i] = min(b[i], mu[i][hi_side].min())
+            if (~hi_side).any():
+                a[i] = max(a[i], mu[i][~hi_side].max())
+        rounds += 1
+        shifts += int(ns.sum())
+    return 0.5 * (a + b), rounds, shifts
+
+
 def kth_group(mats, ks, tol, stream, group=None):
     """lambda_{k_i}(A_i) for every handle in ``mats`` (equal max_lanes and
     precision, all on ``stream``, a torch.cuda.Stream).  Returns (values,
@@ -33,34 +61,21 @@ def kth_group(mats, ks, tol, stream, group=None):
         inf = M.h2_info()
         a[i] = inf["gershgorin_lo"] - 1e-6 * inf["norm_inf"]
         b[i] = inf["gershgorin_hi"] + 1e-6 * inf["norm_inf"]
-    k = np.asarray(ks, dtype=np.int64)
     h_sh = torch.zeros((nh, lanes), dtype=torch.float64).pin_memory()
     h_c = torch.zeros((nh, lanes), dtype=torch.int64).pin_memory()
     d_sh = torch.zeros((nh, lanes), dtype=torch.float64, device="cuda")
     d_c = torch.zeros((nh, lanes), dtype=torch.int64, device="cuda")
-    frac = np.arange(1, lanes + 1) / (lanes + 1.0)
-    rounds = shifts = 0
-    with torch.cuda.stream(stream):
-        while True:
-            act = (b - a) >= tol
-            if not act.any():
-                break
-            mu = a[:, None] + (b - a)[:, None] * frac[None, :]
-            ns = np.where(act, lanes, 0)
+
+    def evaluate(mu, ns):
+        with torch.cuda.stream(stream):
             h_sh.numpy()[:] = mu
             d_sh.copy_(h_sh, non_blocking=True)
             G.h2_group_inertia_device(d_sh, ns, d_c)
             h_c.copy_(d_c, non_blocking=True)
-            stream.synchronize()
-            nu = h_c.numpy()
-            for i in np.nonzero(act)[0]:
-                hi_side = nu[i] >= k[i]
-                if hi_side.any():
-                    b[i] = min(b[i], mu[i][hi_side].min())
-                if (~hi_side).any():
-                    a[i] = max(a[i], mu[i][~hi_side].max())
-            rounds += 1
-            shifts += int(ns.sum())
+        stream.synchronize()
+        return h_c.numpy()
+
+    out = bracket_rounds(a, b, ks, tol, lanes, evaluate)
     if group is None:
         G.close()
-    return 0.5 * (a + b), rounds, shifts
+    return out

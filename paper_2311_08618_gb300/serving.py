@@ -11,13 +11,16 @@ Model
   exceeds the memory reserved for it (admission by HBM footprint).
 * A tick runs one multisection round on every matrix with active requests:
   the distinct active intervals of that matrix share its lanes (q interior
-  points each), the batches of all matrices are enqueued back to back on the
-  server's CUDA stream and waited for once, then every interval of every
-  request is narrowed with all (mu, nu) pairs of its matrix's round
-  (Algorithm 1; inertia reuse across requests, Sec. 4.2).  Requests of one
-  matrix share its batch, so their work overlaps on the device.  (Giving
-  every matrix its own stream stalled the device in testing: all started
-  kernels completed, yet a queued one never started; one stream avoids it.)
+  points each).  When the resident matrices share max_lanes and precision,
+  the round of all of them is one group batch (h2_group: one launch per tree
+  level and colour over all matrices, idle ones with no shifts); otherwise
+  their batches are enqueued back to back on the server's CUDA stream.  The
+  tick waits once, then every interval of every request is narrowed with
+  all (mu, nu) pairs of its matrix's round (Algorithm 1; inertia reuse across
+  requests, Sec. 4.2).  Requests of one matrix share its batch, so their work
+  overlaps on the device.  (Giving every matrix its own stream stalled the
+  device in testing: all started kernels completed, yet a queued one never
+  started; one stream avoids it.)
 * Requests that arrive while others are on the GPU join at the next tick
   (continuous batching).  A new request starts from the tightest bracket in
   its matrix's table of evaluated (mu, nu) pairs instead of the Gershgorin
@@ -34,7 +37,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .binding import H2Matrix, lib
+from .binding import H2Group, H2Matrix, lib
 
 
 @dataclass
@@ -57,6 +60,7 @@ class _Resident:
     h2: H2Matrix
     lanes: int
     stream: object
+    precision: int = 0
     lo0: float
     hi0: float
     table_mu: list = field(default_factory=list)      # sorted evaluated shifts
@@ -66,7 +70,6 @@ class _Resident:
     d_counts: object = None
     h_shifts: object = None
     h_counts: object = None
-    pending: list = field(default_factory=list)        # shifts of the round in flight
 
 
 class Server:
@@ -84,6 +87,8 @@ class Server:
         self.shifts_evaluated = 0
         self.ticks = 0
         self.stream = torch.cuda.Stream()       # one stream for all resident matrices
+        self.group = None                       # group batch over all resident matrices
+        self._group_dirty = True
 
     # -- residency ----------------------------------------------------------
     def add_matrix(self, name, points, kernel, kparams, leaf, rank, eta=1.0, lanes=16, **opts):
@@ -100,7 +105,7 @@ class Server:
         self.footprint += info["workspace_bytes"]
         a = info["gershgorin_lo"] - 1e-6 * info["norm_inf"]
         b = info["gershgorin_hi"] + 1e-6 * info["norm_inf"]
-        r = _Resident(name, h, lanes, stream, a, b)
+        r = _Resident(name, h, lanes, stream, a, b, int(opts.get("precision", 0)))
         r.d_shifts = torch.zeros(lanes, dtype=torch.float64, device="cuda")
         r.d_counts = torch.zeros(lanes, dtype=torch.int64, device="cuda")
         r.h_shifts = torch.zeros(lanes, dtype=torch.float64).pin_memory()
@@ -109,9 +114,36 @@ class Server:
         r.table_mu = [a, b]
         r.table_nu = [0, h.n]
         self.mats[name] = r
+        self._group_dirty = True
         return info
 
+    def _ensure_group(self):
+        """The group of all resident matrices (None if their lanes or
+        precisions differ), with its shift and count buffers."""
+        if not self._group_dirty:
+            return self.group
+        torch = self.torch
+        if self.group is not None:
+            self.group.close()
+            self.group = None
+        mats = list(self.mats.values())
+        lanes = {r.h2.h2_info()["lanes"] for r in mats}
+        opts_ok = len(lanes) == 1 and len({r.precision for r in mats}) == 1
+        if mats and opts_ok:
+            self.group = H2Group([r.h2 for r in mats])
+            L = mats[0].lanes
+            self.g_order = [r.name for r in mats]
+            self.g_hsh = torch.zeros((len(mats), L), dtype=torch.float64).pin_memory()
+            self.g_hc = torch.zeros((len(mats), L), dtype=torch.int64).pin_memory()
+            self.g_dsh = torch.zeros((len(mats), L), dtype=torch.float64, device="cuda")
+            self.g_dc = torch.zeros((len(mats), L), dtype=torch.int64, device="cuda")
+        self._group_dirty = False
+        return self.group
+
     def close(self):
+        if self.group is not None:
+            self.group.close()
+            self.group = None
         for r in self.mats.values():
             r.h2.close()
         self.mats.clear()
@@ -169,8 +201,7 @@ class Server:
     def step(self):
         """Admit, run one multisection round on every busy matrix, update."""
         self._admit()
-        L = lib()
-        launched = []
+        plans = {}
         for r in self.mats.values():
             if not r.active:
                 continue
@@ -189,30 +220,55 @@ class Server:
                 a, b = ivs[u]
                 qu = q + (1 if u < extra else 0)
                 shifts += [a + (b - a) * j / (qu + 1) for j in range(1, qu + 1)]
-            ns = len(shifts)
-            r.h_shifts[:ns] = self.torch.tensor(shifts, dtype=self.torch.float64)
-            r.pending = shifts
-            with self.torch.cuda.stream(r.stream):
-                r.d_shifts[:ns].copy_(r.h_shifts[:ns], non_blocking=True)
-                rc = L.h2_inertia_device(r.h2._h, C.c_void_p(r.d_shifts.data_ptr()), ns,
-                                         C.c_void_p(r.d_counts.data_ptr()), None)
-                if rc != 0:
-                    raise RuntimeError(L.h2_last_error().decode())
-                r.h_counts[:ns].copy_(r.d_counts[:ns], non_blocking=True)
-            launched.append(r)
-        if launched:
+            plans[r.name] = shifts
+        if not plans:
+            self.ticks += 1
+            return 0
+        G = self._ensure_group()
+        results = {}
+        if G is not None:
+            ns = []
+            for i, name in enumerate(self.g_order):
+                sh = plans.get(name, [])
+                ns.append(len(sh))
+                if sh:
+                    self.g_hsh[i, :len(sh)] = self.torch.tensor(sh, dtype=self.torch.float64)
+            with self.torch.cuda.stream(self.stream):
+                self.g_dsh.copy_(self.g_hsh, non_blocking=True)
+                G.h2_group_inertia_device(self.g_dsh, ns, self.g_dc)
+                self.g_hc.copy_(self.g_dc, non_blocking=True)
             self.stream.synchronize()
-        for r in launched:
-            ns = len(r.pending)
-            counts = r.h_counts[:ns].numpy().copy()
-            self.shifts_evaluated += ns
-            for mu, nu in zip(r.pending, counts):
+            hc = self.g_hc.numpy()
+            for i, name in enumerate(self.g_order):
+                if ns[i]:
+                    results[name] = hc[i, :ns[i]].copy()
+        else:
+            L = lib()
+            for name, shifts in plans.items():
+                r = self.mats[name]
+                ns = len(shifts)
+                r.h_shifts[:ns] = self.torch.tensor(shifts, dtype=self.torch.float64)
+                with self.torch.cuda.stream(r.stream):
+                    r.d_shifts[:ns].copy_(r.h_shifts[:ns], non_blocking=True)
+                    rc = L.h2_inertia_device(r.h2._h, C.c_void_p(r.d_shifts.data_ptr()), ns,
+                                             C.c_void_p(r.d_counts.data_ptr()), None)
+                    if rc != 0:
+                        raise RuntimeError(L.h2_last_error().decode())
+                    r.h_counts[:ns].copy_(r.d_counts[:ns], non_blocking=True)
+            self.stream.synchronize()
+            for name, shifts in plans.items():
+                results[name] = self.mats[name].h_counts[:len(shifts)].numpy().copy()
+        for name, shifts in plans.items():
+            r = self.mats[name]
+            counts = results[name]
+            self.shifts_evaluated += len(shifts)
+            for mu, nu in zip(shifts, counts):
                 i = bisect.bisect_left(r.table_mu, mu)
                 r.table_mu.insert(i, mu)
                 r.table_nu.insert(i, int(nu))
             still = []
             for req in r.active:
-                for mu, nu in zip(r.pending, counts):
+                for mu, nu in zip(shifts, counts):
                     if req.lo < mu < req.hi:
                         if nu >= req.k:
                             req.hi = mu
@@ -225,7 +281,7 @@ class Server:
                     still.append(req)
             r.active = still
         self.ticks += 1
-        return len(launched)
+        return len(plans)
 
 
 def run_open_loop(server: Server, arrivals, horizon_s: float, deadline_s: float):

@@ -105,3 +105,26 @@ def test_table_reuse_shortens_later_requests(env):
     assert again.rounds < first.rounds
     assert abs(again.result - first.result) <= 1e-8
     s.close()
+
+
+def test_group_and_separate_batches_agree(env):
+    """The same requests on a server whose matrices share lanes (one group
+    batch per tick) and on one whose lanes differ (per-matrix batches back to
+    back): equal results within tol, and the first server uses a group."""
+    serving = env
+    s1 = _server(serving, ["lap2d", "yuk3d", "cyl"], lanes=8)
+    s2 = serving.Server()
+    for nm, ln in (("lap2d", 8), ("yuk3d", 16), ("cyl", 8)):
+        pts, kind, kp, leaf, rank = MATS[nm]
+        s2.add_matrix(nm, pts(), kind, kp, leaf, rank, lanes=ln)
+    for s in (s1, s2):
+        for m, k, tol in REQS:
+            s.submit(m, k, tol)
+    r1 = sorted(_drain(s1), key=lambda r: r.rid)
+    r2 = sorted(_drain(s2), key=lambda r: r.rid)
+    assert s1.group is not None and s2.group is None
+    assert len(r1) == len(r2) == len(REQS)
+    for a, b in zip(r1, r2):
+        assert abs(a.result - b.result) <= a.tol
+    s1.close()
+    s2.close()
