@@ -1101,6 +1101,18 @@ struct SchurArgs {
 // arithmetic of the products and the type k_trsm stored W, Y in: double (FP64
 // path) or float (mixed path: FP32 products and accumulation, the FP64 block
 // updated by the rounded result).
+// NU rows (ty + 8u, u < NU) of the tile against column tx over kc values of k
+template <typename T, int NU>
+__device__ __forceinline__ void schur_rows(const T (*sR)[TS + 1], const T (*sC)[TS + 1], int kc, int tx, int ty,
+                                           T (&acc)[4]) {
+#pragma unroll 8
+    for (int k = 0; k < kc; ++k) {
+        const T y = sC[tx][k];
+#pragma unroll
+        for (int u = 0; u < NU; ++u) acc[u] += sR[ty + 8 * u][k] * y;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void k_schur_body(const SchurArgs& A, const int bx, const int by) {
     HbScope hb_(5);
@@ -1122,30 +1134,44 @@ __device__ __forceinline__ void k_schur_body(const SchurArgs& A, const int bx, c
     if (i0 >= ra || j0 >= rb) return;
     const T* W = reinterpret_cast<const T*>(scr + A.lay.w + (size_t)P.ta * D * D);
     const T* Y = reinterpret_cast<const T*>(scr + A.lay.y + (size_t)P.tb * D * D);
-    __shared__ T sW[TS][TS + 1], sY[TS][TS + 1];
+    // A warp owns the rows ty + 8u of the tile: rows past the block are not
+    // computed (one warp-uniform choice among four unrolled loops, made once).
+    // Padded columns sit in the lanes and cost as much as real ones, so the
+    // tile is computed transposed when its columns are the more ragged side.
+    const int nr = min(TS, ra - i0), nc = min(TS, rb - j0);
+    const bool tp = nc < nr;
+    const T* Rm = tp ? Y + (size_t)j0 * D : W + (size_t)i0 * D;    // row operand
+    const T* Cm = tp ? W + (size_t)i0 * D : Y + (size_t)j0 * D;    // column operand
+    const int nrow = tp ? nc : nr, ncol = tp ? nr : nc;
+    __shared__ T sR[TS][TS + 1], sC[TS][TS + 1];
     const int tx = threadIdx.x % TS, ty = threadIdx.x / TS;   // ty in 0..7
+    const int nu = max(0, min(4, (nrow - ty + 7) / 8));
     T acc[4] = {0, 0, 0, 0};
     for (int k0 = 0; k0 < Rp; k0 += TS) {
         const int kc = min(TS, Rp - k0);
         for (int e = threadIdx.x; e < TS * TS; e += NT) {
             int r = e / TS, k = e % TS;
-            sW[r][k] = (i0 + r < ra && k < kc) ? W[(size_t)(i0 + r) * D + k0 + k] : (T)0;
-            sY[r][k] = (j0 + r < rb && k < kc) ? Y[(size_t)(j0 + r) * D + k0 + k] : (T)0;
+            sR[r][k] = (r < nrow && k < kc) ? Rm[(size_t)r * D + k0 + k] : (T)0;
+            sC[r][k] = (r < ncol && k < kc) ? Cm[(size_t)r * D + k0 + k] : (T)0;
         }
         __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < kc; ++k) {
-            T y = sY[tx][k];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u] += sW[ty + 8 * u][k] * y;
+        switch (nu) {
+            case 4: schur_rows<T, 4>(sR, sC, kc, tx, ty, acc); break;
+            case 3: schur_rows<T, 3>(sR, sC, kc, tx, ty, acc); break;
+            case 2: schur_rows<T, 2>(sR, sC, kc, tx, ty, acc); break;
+            case 1: schur_rows<T, 1>(sR, sC, kc, tx, ty, acc); break;
+            default: break;
         }
         __syncthreads();
     }
     double* B = slot_ptr(A.slots, P.slot, A.lanes, lane, D);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        int i = i0 + ty + 8 * u, j = j0 + tx;
-        if (i < ra && j < rb) belem(B, D, P.trans, i, j) -= (double)acc[u];
+        const int r = ty + 8 * u;
+        if (r < nrow && tx < ncol) {
+            const int i = tp ? i0 + tx : i0 + r, j = tp ? j0 + r : j0 + tx;
+            belem(B, D, P.trans, i, j) -= (double)acc[u];
+        }
     }
 }
 template <typename T>

@@ -60,9 +60,9 @@ class _Resident:
     h2: H2Matrix
     lanes: int
     stream: object
-    precision: int = 0
     lo0: float
     hi0: float
+    precision: int = 0
     table_mu: list = field(default_factory=list)      # sorted evaluated shifts
     table_nu: list = field(default_factory=list)
     active: list = field(default_factory=list)

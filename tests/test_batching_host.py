@@ -50,3 +50,11 @@ def test_single_lane_is_bisection():
                                     - (mu < -1.0))
     assert abs(mid[0] - 0.25) < 5e-7
     assert rounds == int(np.ceil(np.log2(6.0 / 1e-6)))
+
+
+def test_package_modules_import_without_a_gpu():
+    """Every module of the package imports on a CPU-only host (the library
+    itself is loaded only when a call needs it)."""
+    import importlib
+    for m in ("binding", "batching", "serving", "sharding", "build"):
+        importlib.import_module("paper_2311_08618_gb300." + m)
