@@ -969,75 +969,147 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
                   8.0 * 3.0 * rows * (double)Rp);
     }
     if (rows <= 0) return;
-    // L, D and the pivots: staged in shared memory (as T) when they fit
-    const double* F = scr + A.lay.f;
-    const int* perm = (const int*)(scr + A.lay.iperm);
-    const int* piv = perm + D;
-    const T* sL = nullptr;
-    const int* sperm = perm;
-    const int* spiv = piv;
-    if (use_smem) {
-        T* L2 = reinterpret_cast<T*>(sh);                        // Rp x Rp
-        int* p2 = reinterpret_cast<int*>(L2 + (size_t)Rp * Rp);
-        int* v2 = p2 + Rp;
-        for (int e = threadIdx.x; e < Rp * Rp; e += NT) L2[e] = (T)F[(size_t)(e / Rp) * D + e % Rp];
-        for (int e = threadIdx.x; e < Rp; e += NT) { p2[e] = perm[e]; v2[e] = piv[e]; }
-        sL = L2;
-        sperm = p2;
-        spiv = v2;
-    }
-    __syncthreads();
-    auto Fx = [&](int j, int k) -> T {  // entry (j, k) of the packed factor
-        return use_smem ? sL[(size_t)j * Rp + k] : (T)F[(size_t)j * D + k];
-    };
-    auto Lx = [&](int j, int k) -> T {  // L(j, k), k < j, of the unit lower factor
-        return (spiv[k] == 2 && j == k + 1) ? (T)0 : Fx(j, k);
-    };
     const int tr = A.targ_trans[ci * A.ntarg_max + ti];
     const double* B = slot_ptr(A.slots, A.targ_slot[ci * A.ntarg_max + ti], LN, lane, D);
     T* W = reinterpret_cast<T*>(scr + A.lay.w + (size_t)ti * D * D);
     T* Y = reinterpret_cast<T*>(scr + A.lay.y + (size_t)ti * D * D);
-    for (int e = threadIdx.x; e < rows * Rp; e += NT) {       // W = S_ap^{.R} P
-        int i = e / Rp, j = e % Rp;
-        W[(size_t)i * D + j] = (T)(tr ? B[(size_t)(rk1 + sperm[j]) * D + i] : B[(size_t)i * D + rk1 + sperm[j]]);
-    }
-    __syncthreads();
-    for (int jb = 0; jb < Rp; jb += JB) {
-        const int nb = min(JB, Rp - jb);
-        if (jb > 0) {
-            for (int e = threadIdx.x; e < rows * nb; e += NT) {
-                int i = e / nb, j = jb + e % nb;
-                T v = W[(size_t)i * D + j];
-                const T* wi = W + (size_t)i * D;
-                for (int k = 0; k < jb; ++k) v -= wi[k] * Lx(j, k);
-                W[(size_t)i * D + j] = v;
+    if (use_smem == 2) {
+        // everything in shared memory: L with the (k+1, k) entries of 2x2
+        // pivots read as 0 (they hold D's off-diagonal), D's diagonal and
+        // off-diagonal apart, and W; the same expressions as the path below
+        const double* F = scr + A.lay.f;
+        const int* perm = (const int*)(scr + A.lay.iperm);
+        const int* piv = perm + D;
+        T* sLz = reinterpret_cast<T*>(sh);                       // Rp x Rp
+        T* sWm = sLz + (size_t)Rp * Rp;                          // rows x (Rp + 1)
+        T* sDg = sWm + (size_t)rows * (Rp + 1);
+        T* sOd = sDg + Rp;
+        int* sPerm = reinterpret_cast<int*>(sOd + Rp);
+        int* sPiv = sPerm + Rp;
+        const int ldw = Rp + 1;
+        for (int e = threadIdx.x; e < Rp * Rp; e += NT) {
+            const int j = e / Rp, k = e % Rp;
+            sLz[e] = (k < j && !(piv[k] == 2 && j == k + 1)) ? (T)F[(size_t)j * D + k] : (T)0;
+        }
+        for (int j = threadIdx.x; j < Rp; j += NT) {
+            sDg[j] = (T)F[(size_t)j * D + j];
+            sOd[j] = (piv[j] == 2 && j + 1 < Rp) ? (T)F[(size_t)(j + 1) * D + j] : (T)0;
+            sPerm[j] = perm[j];
+            sPiv[j] = piv[j];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * Rp; e += NT) {      // W = S_ap^{.R} P
+            const int i = e / Rp, j = e % Rp;
+            sWm[i * ldw + j] = (T)(tr ? B[(size_t)(rk1 + sPerm[j]) * D + i] : B[(size_t)i * D + rk1 + sPerm[j]]);
+        }
+        __syncthreads();
+        for (int jb = 0; jb < Rp; jb += JB) {
+            const int nb = min(JB, Rp - jb);
+            if (jb > 0) {
+                for (int e = threadIdx.x; e < rows * nb; e += NT) {
+                    const int i = e / nb, j = jb + e % nb;
+                    const T* wi = sWm + i * ldw;
+                    const T* lj = sLz + (size_t)j * Rp;
+                    T v = wi[j];
+                    for (int k = 0; k < jb; ++k) v -= wi[k] * lj[k];
+                    sWm[i * ldw + j] = v;
+                }
+                __syncthreads();
+            }
+            for (int i = threadIdx.x; i < rows; i += NT) {
+                T* wi = sWm + i * ldw;
+                for (int j = jb + 1; j < jb + nb; ++j) {
+                    const T* lj = sLz + (size_t)j * Rp;
+                    T v = wi[j];
+                    for (int k = jb; k < j; ++k) v -= wi[k] * lj[k];
+                    wi[j] = v;
+                }
             }
             __syncthreads();
         }
-        for (int i = threadIdx.x; i < rows; i += NT) {
-            T* wi = W + (size_t)i * D;
-            for (int j = jb + 1; j < jb + nb; ++j) {
-                T v = wi[j];
-                for (int k = jb; k < j; ++k) v -= wi[k] * Lx(j, k);
-                wi[j] = v;
+        for (int e = threadIdx.x; e < rows * Rp; e += NT) {       // Y = W D^{-1}
+            const int i = e / Rp, j = e % Rp;
+            const T* wi = sWm + i * ldw;
+            T v;
+            if (sPiv[j] == 1) {
+                v = wi[j] * ((T)1 / sDg[j]);
+            } else {
+                const int j0 = sPiv[j] == 2 ? j : j - 1;
+                const T a0 = sDg[j0], b0 = sOd[j0], c0 = sDg[j0 + 1];
+                const T idet = (T)1 / (a0 * c0 - b0 * b0);
+                const T w0 = wi[j0], w1 = wi[j0 + 1];
+                v = (j == j0) ? (w0 * c0 - w1 * b0) * idet : (w1 * a0 - w0 * b0) * idet;
             }
+            Y[(size_t)i * D + j] = v;
+            W[(size_t)i * D + j] = wi[j];
+        }
+    } else {
+        // L, D and the pivots: staged in shared memory (as T) when they fit
+        const double* F = scr + A.lay.f;
+        const int* perm = (const int*)(scr + A.lay.iperm);
+        const int* piv = perm + D;
+        const T* sL = nullptr;
+        const int* sperm = perm;
+        const int* spiv = piv;
+        if (use_smem) {
+            T* L2 = reinterpret_cast<T*>(sh);                        // Rp x Rp
+            int* p2 = reinterpret_cast<int*>(L2 + (size_t)Rp * Rp);
+            int* v2 = p2 + Rp;
+            for (int e = threadIdx.x; e < Rp * Rp; e += NT) L2[e] = (T)F[(size_t)(e / Rp) * D + e % Rp];
+            for (int e = threadIdx.x; e < Rp; e += NT) { p2[e] = perm[e]; v2[e] = piv[e]; }
+            sL = L2;
+            sperm = p2;
+            spiv = v2;
         }
         __syncthreads();
-    }
-    for (int e = threadIdx.x; e < rows * Rp; e += NT) {       // Y = W D^{-1}
-        int i = e / Rp, j = e % Rp;
-        const T* wi = W + (size_t)i * D;
-        T v;
-        if (spiv[j] == 1) {
-            v = wi[j] * ((T)1 / Fx(j, j));
-        } else {
-            int j0 = spiv[j] == 2 ? j : j - 1;
-            T a0 = Fx(j0, j0), b0 = Fx(j0 + 1, j0), c0 = Fx(j0 + 1, j0 + 1);
-            T idet = (T)1 / (a0 * c0 - b0 * b0);
-            T w0 = wi[j0], w1 = wi[j0 + 1];
-            v = (j == j0) ? (w0 * c0 - w1 * b0) * idet : (w1 * a0 - w0 * b0) * idet;
+        auto Fx = [&](int j, int k) -> T {  // entry (j, k) of the packed factor
+            return use_smem ? sL[(size_t)j * Rp + k] : (T)F[(size_t)j * D + k];
+        };
+        auto Lx = [&](int j, int k) -> T {  // L(j, k), k < j, of the unit lower factor
+            return (spiv[k] == 2 && j == k + 1) ? (T)0 : Fx(j, k);
+        };
+        for (int e = threadIdx.x; e < rows * Rp; e += NT) {       // W = S_ap^{.R} P
+            int i = e / Rp, j = e % Rp;
+            W[(size_t)i * D + j] = (T)(tr ? B[(size_t)(rk1 + sperm[j]) * D + i] : B[(size_t)i * D + rk1 + sperm[j]]);
         }
-        Y[(size_t)i * D + j] = v;
+        __syncthreads();
+        for (int jb = 0; jb < Rp; jb += JB) {
+            const int nb = min(JB, Rp - jb);
+            if (jb > 0) {
+                for (int e = threadIdx.x; e < rows * nb; e += NT) {
+                    int i = e / nb, j = jb + e % nb;
+                    T v = W[(size_t)i * D + j];
+                    const T* wi = W + (size_t)i * D;
+                    for (int k = 0; k < jb; ++k) v -= wi[k] * Lx(j, k);
+                    W[(size_t)i * D + j] = v;
+                }
+                __syncthreads();
+            }
+            for (int i = threadIdx.x; i < rows; i += NT) {
+                T* wi = W + (size_t)i * D;
+                for (int j = jb + 1; j < jb + nb; ++j) {
+                    T v = wi[j];
+                    for (int k = jb; k < j; ++k) v -= wi[k] * Lx(j, k);
+                    wi[j] = v;
+                }
+            }
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < rows * Rp; e += NT) {       // Y = W D^{-1}
+            int i = e / Rp, j = e % Rp;
+            const T* wi = W + (size_t)i * D;
+            T v;
+            if (spiv[j] == 1) {
+                v = wi[j] * ((T)1 / Fx(j, j));
+            } else {
+                int j0 = spiv[j] == 2 ? j : j - 1;
+                T a0 = Fx(j0, j0), b0 = Fx(j0 + 1, j0), c0 = Fx(j0 + 1, j0 + 1);
+                T idet = (T)1 / (a0 * c0 - b0 * b0);
+                T w0 = wi[j0], w1 = wi[j0 + 1];
+                v = (j == j0) ? (w0 * c0 - w1 * b0) * idet : (w1 * a0 - w0 * b0) * idet;
+            }
+            Y[(size_t)i * D + j] = v;
+        }
     }
     if (A.lay.dk > 0) {          // FP64_TC: digit planes of W_a and Y_a, once
         __syncthreads();
@@ -1958,12 +2030,15 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
             }
             {
                 const size_t sm_trsm = (size_t)Dm * Dm * sizeof(double) + 2 * (size_t)Dm * sizeof(int);
+                // flag 2: L, D and W staged (Rp^2 + rows (Rp + 1) + 2 Rp values, 2 Rp ints)
+                const size_t sm_full = ((size_t)Dm * Dm + (size_t)Dm * (Dm + 1) + 2 * (size_t)Dm) * sizeof(double) +
+                                       2 * (size_t)Dm * sizeof(int);
                 LaunchRec q = r;
                 q.op = OP_TRSM;
                 q.kind = H2_KIND_TRSM;
-                q.flag = sm_trsm <= kSmemCap ? 1 : 0;
+                q.flag = sm_full <= kSmemCap ? 2 : (sm_trsm <= kSmemCap ? 1 : 0);
                 q.variant = mixed ? 1 : 0;
-                q.smem = q.flag ? sm_trsm : 0;
+                q.smem = q.flag == 2 ? sm_full : (q.flag ? sm_trsm : 0);
                 q.grid = dim3(C.ncl * C.ntarg_max, LN);
                 R.push_back(q);
             }
