@@ -367,6 +367,19 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
     lat = np.array(lat[2:])
     info2 = Me.h2_info()
     Me.close()
+    # ---- all n eigenvalues in one call (spectrum slicing with the reuse of
+    # every (mu, nu) for every k, Sec. 4.2), on the throughput handle
+    all_eigs = None
+    if args.all_eigs and WORKLOAD["n"] <= 8192:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lam_all, eb_all = M.h2_kth_eig(np.arange(1, WORKLOAD["n"] + 1), WORKLOAD["tol"])
+        t_all = time.perf_counter() - t0
+        inf_all = M.h2_info()
+        all_eigs = {"k": "1..%d" % WORKLOAD["n"], "tol": WORKLOAD["tol"], "lanes": lanes, "seconds": t_all,
+                    "eigs_per_s": WORKLOAD["n"] / t_all, "rounds": inf_all["last_rounds"],
+                    "shifts": inf_all["last_shifts"], "max_err_bound": float(eb_all.max()),
+                    "sorted": bool(np.all(np.diff(lam_all) >= 0))}
     # ---- roofline of the dominant kernel: profiled batches (events per launch)
     prof = None
     for i in range(args.warmup, min(total, args.warmup + 5)):
@@ -517,7 +530,8 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
                      "rounds": info2["last_rounds"], "shifts_per_solve": info2["last_shifts"],
                      "lambda": lam[0], "err_bound": lam[1]},
             "build_s": build_s, "roofline": roof, "clocks": clocks, "precision": precision,
-            "fp64_tc": fp64_tc, "plain_fp64": plain, "serving": serving_res, "batching": batching_res}
+            "all_eigs": all_eigs, "fp64_tc": fp64_tc, "plain_fp64": plain, "serving": serving_res,
+            "batching": batching_res}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         sample = list(sh[args.warmup][:: max(1, lanes // (2 * cores))][:2 * cores])
@@ -659,6 +673,7 @@ def main():
     ap.add_argument("--serving-sustain-rate", type=float, default=2.0, help="second, sustainable rate (0: skip)")
     ap.add_argument("--serving-sustain-s", type=float, default=5.0)
     ap.add_argument("--batch-count", type=int, default=24, help="matrices of the batching sample (0: skip)")
+    ap.add_argument("--all-eigs", type=int, default=1, help="1: also solve for all n eigenvalues (n <= 8192)")
     ap.add_argument("--batch-nmax", type=int, default=8192)
     ap.add_argument("--batch-lanes", type=int, default=4)
     ap.add_argument("--serving-lanes", type=int, default=16)

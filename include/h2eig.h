@@ -215,7 +215,9 @@ void h2_group_destroy(h2_group g);
  * interval of width < tol found by bisection/multisection from the Gershgorin
  * interval (|lambda_k - lambda~_k| < tol/2, Eq. error-bound).  Every evaluated
  * (mu, nu) narrows every k (Sec. 4.2); each round spreads max_lanes shifts
- * over the distinct active intervals.  The intervals stay on the device.
+ * over the distinct active intervals, the first max_lanes of them in k order
+ * (any number of k, in any order, repeats allowed: up to all n eigenvalues in
+ * one call).  The intervals stay on the device.
  * H2_PREC_MIXED: mixed rounds (guarded as in h2_inertia) run while the
  * brackets are wider than Delta = 64 * 2^-24 * ||A||_inf; every bracket is
  * then widened by Delta and checked in FP64 (nu(lo) < k <= nu(hi), else it

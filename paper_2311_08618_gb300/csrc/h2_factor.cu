@@ -1696,6 +1696,7 @@ struct FactorState {
     double* d_hi = nullptr;
     int64_t* d_k = nullptr;
     int* d_nact = nullptr;
+    int* d_first = nullptr;   // [lanes]: the intervals of a round
     int nk_cap = 0;
 };
 
@@ -2615,34 +2616,61 @@ int run_inertia_host(h2_matrix* h, const double* shifts, int64_t ns, int64_t* co
 // --------------------------------------------------------------- bisection --
 // plan: distinct active intervals get the lanes; each gets q points
 // lo + (hi-lo) j/(q+1), j = 1..q
-__global__ void k_bisect_plan(const double* lo, const double* hi, int nk, double tol, int lanes,
-                              double* shifts, int* active, int* nact) {
-    __shared__ int s_first[1024];
-    // distinct active intervals in k order (O(nk^2) dedupe, nk small)
-    if (threadIdx.x == 0) {
-        int nd = 0;
-        for (int k = 0; k < nk; ++k) {
-            if (!(hi[k] - lo[k] >= tol)) continue;
-            bool dup = false;
-            for (int u = 0; u < nd && !dup; ++u) {
-                int k2 = s_first[u];
-                dup = (lo[k2] == lo[k] && hi[k2] == hi[k]);
-            }
-            if (!dup && nd < 1024) s_first[nd++] = k;
+// Plan of one multisection round over nk brackets sorted by k.  Brackets of
+// sorted k narrowed by the same (mu, nu) pairs are monotone in k, so equal
+// brackets are adjacent and the first of each run is a distinct interval (a
+// missed duplicate would only repeat work).  One CTA scans the brackets in
+// chunks (block prefix sums), keeps the first `lanes` distinct intervals
+// wider than tol in k order and spreads the lanes over them: interval u gets
+// q or q + 1 equally spaced interior points.
+__global__ void __launch_bounds__(1024) k_bisect_plan(const double* lo, const double* hi, int nk, double tol,
+                                                      int lanes, double* shifts, int* active, int* nact,
+                                                      int* first) {
+    __shared__ int wsum[32];
+    __shared__ int s_base;
+    const int t = threadIdx.x, w = t >> 5, l = t & 31, nw = (blockDim.x + 31) >> 5;
+    if (t == 0) s_base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nk; c0 += blockDim.x) {
+        const int k = c0 + t;
+        int f = 0;
+        if (k < nk && hi[k] - lo[k] >= tol) f = (k == 0 || !(lo[k - 1] == lo[k] && hi[k - 1] == hi[k])) ? 1 : 0;
+        int incl = f;                                   // inclusive scan within the warp
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (l >= o) incl += v;
         }
+        if (l == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            int v = l < nw ? wsum[l] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                int u = __shfl_up_sync(0xffffffffu, v, o);
+                if (l >= o) v += u;
+            }
+            if (l < nw) wsum[l] = v;                    // inclusive warp prefix
+        }
+        __syncthreads();
+        const int before = s_base + (w > 0 ? wsum[w - 1] : 0) + incl - f;
+        if (f && before < lanes) first[before] = k;
+        __syncthreads();
+        if (t == 0) s_base += wsum[nw - 1];
+        __syncthreads();
+    }
+    const int nd = s_base;
+    if (t == 0) {
         *nact = nd;
-        int used = 0;
-        if (nd > 0) {
-            int m = min(nd, lanes);
-            int q = lanes / m, extra = lanes % m;
-            for (int u = 0; u < m; ++u) {
-                int qu = q + (u < extra ? 1 : 0);
-                int k = s_first[u];
-                double a = lo[k], b = hi[k];
-                for (int j = 1; j <= qu; ++j) shifts[used++] = a + (b - a) * (double)j / (double)(qu + 1);
-            }
-        }
-        *active = used;
+        *active = nd > 0 ? lanes : 0;
+    }
+    const int m = min(nd, lanes);
+    if (m == 0) return;
+    const int q = lanes / m, extra = lanes % m;
+    for (int u = t; u < m; u += blockDim.x) {
+        const int qu = q + (u < extra ? 1 : 0);
+        const int off = u * q + min(u, extra);
+        const int k = first[u];
+        const double a = lo[k], b = hi[k];
+        for (int j = 1; j <= qu; ++j) shifts[off + j - 1] = a + (b - a) * (double)j / (double)(qu + 1);
     }
 }
 
@@ -2675,7 +2703,8 @@ static int kth_round(h2_matrix* h, int nk, double width, int mixed, int guard, i
     Workspace& ws = h->ws;
     FactorState* fs = state_of(h);
     cudaStream_t st = h->stream;
-    k_bisect_plan<<<1, 32, 0, st>>>(fs->d_lo, fs->d_hi, nk, width, ws.lanes, ws.d_shifts, fs->d_active, fs->d_nact);
+    k_bisect_plan<<<1, 1024, 0, st>>>(fs->d_lo, fs->d_hi, nk, width, ws.lanes, ws.d_shifts, fs->d_active, fs->d_nact,
+                                      fs->d_first);
     int used = 0;
     CK(cudaMemcpyAsync(nact, fs->d_nact, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&used, fs->d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -2710,10 +2739,13 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
     FactorState* fs = state_of(h);
     cudaStream_t st = h->stream;
     int rc;
-    if (nk > 1024) {
-        set_error("h2_kth_eig: at most 1024 k per call");
-        return H2_ERR_INVALID_ARG;
-    }
+    // brackets in k order (equal brackets adjacent, see k_bisect_plan); the
+    // results go back to the caller's order
+    std::vector<int64_t> order(nk), ks(nk);
+    for (int64_t i = 0; i < nk; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return k[x] < k[y]; });
+    for (int64_t i = 0; i < nk; ++i) ks[i] = k[order[i]];
+    k = ks.data();
     CK(cudaMemsetAsync(ws.d_err, 0, 8 * sizeof(int), st));
     // start interval: Gershgorin padded by 1e-6 ||A||_inf; check nu(a) = 0, nu(b) = n in FP64
     const double a = h->glo - 1e-6 * h->norm_inf, b = h->ghi + 1e-6 * h->norm_inf;
@@ -2727,9 +2759,13 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
         }
     }
     if (fs->nk_cap < nk) {
-        cudaFree(fs->d_lo); cudaFree(fs->d_hi); cudaFree(fs->d_k); cudaFree(fs->d_nact);
+        cudaFree(fs->d_lo); cudaFree(fs->d_hi); cudaFree(fs->d_k); cudaFree(fs->d_nact); cudaFree(fs->d_first);
+        fs->d_lo = fs->d_hi = nullptr;
+        fs->d_k = nullptr;
+        fs->d_nact = fs->d_first = nullptr;
+        fs->nk_cap = 0;
         if ((rc = dalloc(&fs->d_lo, nk)) || (rc = dalloc(&fs->d_hi, nk)) || (rc = dalloc(&fs->d_k, nk)) ||
-            (rc = dalloc(&fs->d_nact, 1)))
+            (rc = dalloc(&fs->d_nact, 1)) || (rc = dalloc(&fs->d_first, ws.lanes)))
             return rc;
         fs->nk_cap = (int)nk;
     }
@@ -2807,8 +2843,8 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
         return H2_ERR_NUMERICAL;
     }
     for (int64_t i = 0; i < nk; ++i) {
-        out[i] = 0.5 * (lo[i] + hi[i]);
-        if (err_bound) err_bound[i] = 0.5 * (hi[i] - lo[i]);
+        out[order[i]] = 0.5 * (lo[i] + hi[i]);
+        if (err_bound) err_bound[order[i]] = 0.5 * (hi[i] - lo[i]);
     }
     return H2_OK;
 }
@@ -2836,7 +2872,7 @@ void free_workspace(h2_matrix* h) {
             cudaFree(W.d_slot_of); cudaFree(W.d_far_of);
         }
         cudaFree(fs->d_active); cudaFree(fs->d_counts); cudaFree(fs->d_mp); cudaFree(fs->d_stats);
-        cudaFree(fs->d_lo); cudaFree(fs->d_hi); cudaFree(fs->d_k); cudaFree(fs->d_nact);
+        cudaFree(fs->d_lo); cudaFree(fs->d_hi); cudaFree(fs->d_k); cudaFree(fs->d_nact); cudaFree(fs->d_first);
         delete fs;
     }
     ws.graph_state = nullptr;
