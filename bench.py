@@ -550,6 +550,46 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
 SERVING_SIZES = (1024, 2048, 4096, 8192)
 
 
+def _circle_sweep(args):
+    """The paper's scaling experiment (Sec. 5.1): A_ij = 1/(|x_i - x_j| + 1e-3)
+    on n points uniformly distributed on the unit circle, the k = n/2
+    eigenvalue to eps_ev = 1e-5 from the constant starting interval [0, 2048]
+    (checked: nu(0) < k <= nu(2048)), eps_H2 = 1e-2 eps_ev (relative to
+    ||A||_inf), leaf 64, rank cap 32, FP64, --circle-lanes shifts per round.
+    Prints one JSON line per run (not the bench line)."""
+    import torch
+    import paper_2311_08618_gb300 as pkg
+    from paper_2311_08618_gb300 import batching
+    st = torch.cuda.Stream()
+    out = []
+    for n in [int(v) for v in args.circle_sweep.split(",")]:
+        X = W.unit_circle(n, 5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        M = pkg.H2Matrix(X, W.LAPLACE_EPS, (1e-3, 0, 0, 0), leaf=64, rank=32, eta=1.0, eps_h2=1e-7,
+                         max_lanes=args.circle_lanes, stream=st.cuda_stream)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        info = M.h2_info()
+        k = n // 2
+        c, _ = M.h2_inertia([0.0, 2048.0])
+        rec = {"n": n, "build_s": build_s, "workspace_GB": info["workspace_bytes"] / 1e9,
+               "max_rank": info["max_rank"], "levels": info["levels"], "nu_0": int(c[0]), "nu_2048": int(c[1])}
+        if c[0] < k <= c[1]:
+            G = pkg.H2Group([M])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lam, rounds, shifts = batching.kth_group([M], [k], 1e-5, st, G, start=([0.0], [2048.0]))
+            sec = time.perf_counter() - t0
+            rec.update({"lambda_k": float(lam[0]), "seconds": sec, "rounds": rounds, "shifts": shifts,
+                        "ms_per_shift": 1e3 * sec / shifts})
+            G.close()
+        M.close()
+        out.append(rec)
+        print(json.dumps({"circle_sweep_point": rec}), flush=True)
+    return out
+
+
 def _tune_summary(mats):
     """(levels with one warp per Bunch-Kaufman block, levels with a clustered
     recompression) / levels, over all handles."""
@@ -674,6 +714,8 @@ def main():
     ap.add_argument("--serving-sustain-s", type=float, default=5.0)
     ap.add_argument("--batch-count", type=int, default=24, help="matrices of the batching sample (0: skip)")
     ap.add_argument("--all-eigs", type=int, default=1, help="1: also solve for all n eigenvalues (n <= 8192)")
+    ap.add_argument("--circle-sweep", default="", help="comma-separated n: run the unit-circle scaling sweep only")
+    ap.add_argument("--circle-lanes", type=int, default=4)
     ap.add_argument("--batch-nmax", type=int, default=8192)
     ap.add_argument("--batch-lanes", type=int, default=4)
     ap.add_argument("--serving-lanes", type=int, default=16)
@@ -688,6 +730,8 @@ def main():
     try:
         if args.impl == "reference":
             reference_arm(args, rank, world, dist)
+        elif args.circle_sweep:
+            _circle_sweep(args)
         else:
             ours(args, rank, world, local, dist)
     finally:

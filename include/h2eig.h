@@ -61,6 +61,9 @@ typedef struct {
 /* ---- options ------------------------------------------------------------ */
 #define H2_ADM_BOX    0  /* max(diam c, diam d) <= eta * dist(box c, box d) */
 #define H2_ADM_CENTER 1  /* (diam c + diam d)/2 <= eta * |center c - center d| */
+#define H2_ADM_WEAK   2  /* every pair of distinct clusters (HSS, Sec. 3.3): only
+                            diagonal blocks stay dense, no fill-ins, one colour per
+                            level; eta is ignored */
 
 #define H2_PREC_FP64  0  /* every step in FP64 */
 #define H2_PREC_MIXED 1  /* Schur-update, triangular-solve and rotation
@@ -78,7 +81,7 @@ typedef struct {
 typedef struct {
     int precision;       /* H2_PREC_FP64 (default), H2_PREC_MIXED or
                             H2_PREC_FP64_TC */
-    int admissibility;   /* H2_ADM_BOX (default) or H2_ADM_CENTER */
+    int admissibility;   /* H2_ADM_BOX (default), H2_ADM_CENTER or H2_ADM_WEAK */
     double eps_h2;       /* truncation tolerance relative to ||A||_inf (Sec. 3.1,
                             eps_H2; default 1e-10 = 1e-2 * 1e-8, Sec. 5) */
     int fill_cap;        /* max skeleton columns per cluster after fill-in

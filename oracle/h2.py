@@ -13,7 +13,9 @@ Readings taken where the paper is silent (each also listed in the design notes):
   depth L = ceil(log2(n / leaf)).
 * Admissibility of a cluster pair (c, d), c != d, on point bounding boxes:
   ADM_BOX    max(diam c, diam d) <= eta * dist(box c, box d);
-  ADM_CENTER (diam c + diam d) / 2 <= eta * |center c - center d|.
+  ADM_CENTER (diam c + diam d) / 2 <= eta * |center c - center d|;
+  ADM_WEAK   always (weak admissibility: the HSS structure of Sec. 3.3, where
+             every off-diagonal block is low-rank; no fill-ins arise).
   The block tree is built top-down from the root pair; a leaf pair that is not
   admissible is "near" (dense).
 * Fill-in closure: eliminating cluster p updates every pair (a, b) of its near
@@ -58,7 +60,7 @@ from scipy.linalg import solve_triangular
 from . import dense
 from workloads import splitmix64
 
-ADM_BOX, ADM_CENTER = 0, 1
+ADM_BOX, ADM_CENTER, ADM_WEAK = 0, 1, 2
 
 
 # ----------------------------------------------------------------------------
@@ -120,6 +122,8 @@ def admissible(lo, hi, c, d, eta, rule):
     """Strong admissibility of the cluster pair (c, d) (readings above)."""
     if c == d:
         return False
+    if rule == ADM_WEAK:
+        return True
     dc = math.sqrt(float(np.sum((hi[c] - lo[c]) ** 2)))
     dd = math.sqrt(float(np.sum((hi[d] - lo[d]) ** 2)))
     if rule == ADM_BOX:

@@ -9,5 +9,5 @@ names.  There is no CPU fallback: loading fails loudly without the library.
 from .binding import (  # noqa: F401
     H2Error, H2Group, H2Matrix, Kernel, Options, lib, library_path,
     H2_K_LAPLACE_EPS, H2_K_YUKAWA_EPS, H2_K_GAUSS_PLUS_INV, H2_K_TRIDIAG_TEST, H2_K_MIN_TEST,
-    H2_ADM_BOX, H2_ADM_CENTER, H2_PREC_FP64, H2_PREC_MIXED, H2_PREC_FP64_TC, EXPORTED_SYMBOLS,
+    H2_ADM_BOX, H2_ADM_CENTER, H2_ADM_WEAK, H2_PREC_FP64, H2_PREC_MIXED, H2_PREC_FP64_TC, EXPORTED_SYMBOLS,
 )

@@ -47,10 +47,11 @@ def bracket_rounds(a, b, ks, tol, lanes, evaluate):
     return 0.5 * (a + b), rounds, shifts
 
 
-def kth_group(mats, ks, tol, stream, group=None):
+def kth_group(mats, ks, tol, stream, group=None, start=None):
     """lambda_{k_i}(A_i) for every handle in ``mats`` (equal max_lanes and
-    precision, all on ``stream``, a torch.cuda.Stream).  Returns (values,
-    rounds, shifts evaluated)."""
+    precision, all on ``stream``, a torch.cuda.Stream).  ``start`` = (a, b)
+    replaces the widened Gershgorin intervals (the caller guarantees
+    nu(a_i) < k_i <= nu(b_i)).  Returns (values, rounds, shifts evaluated)."""
     import torch
     G = group if group is not None else H2Group(mats)
     nh = len(mats)
@@ -61,6 +62,9 @@ def kth_group(mats, ks, tol, stream, group=None):
         inf = M.h2_info()
         a[i] = inf["gershgorin_lo"] - 1e-6 * inf["norm_inf"]
         b[i] = inf["gershgorin_hi"] + 1e-6 * inf["norm_inf"]
+    if start is not None:
+        a[:] = start[0]
+        b[:] = start[1]
     h_sh = torch.zeros((nh, lanes), dtype=torch.float64).pin_memory()
     h_c = torch.zeros((nh, lanes), dtype=torch.int64).pin_memory()
     d_sh = torch.zeros((nh, lanes), dtype=torch.float64, device="cuda")

@@ -14,7 +14,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 H2_K_LAPLACE_EPS, H2_K_YUKAWA_EPS, H2_K_GAUSS_PLUS_INV, H2_K_TRIDIAG_TEST, H2_K_MIN_TEST = 0, 1, 2, 3, 4
-H2_ADM_BOX, H2_ADM_CENTER = 0, 1
+H2_ADM_BOX, H2_ADM_CENTER, H2_ADM_WEAK = 0, 1, 2
 H2_PREC_FP64, H2_PREC_MIXED, H2_PREC_FP64_TC = 0, 1, 2
 
 EXPORTED_SYMBOLS = ["h2_default_options", "h2_build", "h2_destroy", "h2_last_error", "h2_inertia",

@@ -62,7 +62,7 @@ int h2_build(const double* points, int64_t n, int d, h2_kernel kernel, int leaf,
     if (!(o.pivot_guard > 0.0)) o.pivot_guard = 1e-4;
     if (!(o.eps_h2 >= 0.0) || o.fill_cap < 0 || o.sketch_cols < 0 ||
         (o.precision != H2_PREC_FP64 && o.precision != H2_PREC_MIXED && o.precision != H2_PREC_FP64_TC) ||
-        (o.admissibility != H2_ADM_BOX && o.admissibility != H2_ADM_CENTER)) {
+        (o.admissibility != H2_ADM_BOX && o.admissibility != H2_ADM_CENTER && o.admissibility != H2_ADM_WEAK)) {
         set_error("h2_build: invalid options");
         return H2_ERR_INVALID_ARG;
     }

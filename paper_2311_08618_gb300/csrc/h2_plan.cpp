@@ -4,7 +4,9 @@
 //  * binary tree, median split along the longest bounding-box axis (first axis
 //    on ties), stable order by that coordinate; all leaves at depth
 //    L = ceil(log2(n / leaf));
-//  * strong admissibility on point bounding boxes (H2_ADM_BOX or H2_ADM_CENTER);
+//  * strong admissibility on point bounding boxes (H2_ADM_BOX or H2_ADM_CENTER), or
+//    weak admissibility (H2_ADM_WEAK: every pair of distinct clusters, the HSS
+//    structure of Sec. 3.3);
 //    the block tree is refined top-down from the root pair;
 //  * every pair of near neighbours of a cluster receives a Schur update when
 //    that cluster is eliminated (Eq. blr2-diag-schur on dense off-diagonal
@@ -37,6 +39,7 @@ double diam(const Box& b, int d) {
 }
 
 bool admissible(const Box& a, const Box& b, int d, double eta, int rule) {
+    if (rule == H2_ADM_WEAK) return true;   // every pair of distinct clusters (HSS)
     double da = diam(a, d), db = diam(b, d);
     if (rule == H2_ADM_BOX) {
         double s = 0.0;

@@ -182,3 +182,48 @@ def test_sketch_matrix_moments():
     Om = h2.sketch_matrix(4000, 8, 3)
     assert np.allclose(Om.T @ Om / 4000 * 8, np.eye(8), atol=0.1)
     assert np.all(np.abs(Om) <= math.sqrt(3.0 / 8))
+
+
+# ---- weak admissibility (HSS structure, Sec. 3.3) ---------------------------
+@pytest.mark.parametrize("n,leaf", [(64, 8), (100, 16)])
+def test_weak_tridiagonal_exact(n, leaf):
+    """Under weak admissibility every off-diagonal block is far; a cluster's
+    far row of the (2, -1) tridiagonal holds its first and last point's -1
+    entries (rank 2, exact).  Counts equal the closed form; no fill-ins, one
+    colour per level."""
+    h = h2.construct(W.line_points(n), W.TRIDIAG_TEST, (0, 0, 0, 0), leaf, 4, 1.0, rule=h2.ADM_WEAK)
+    assert h.stats["max_rank"] == 2 and h.stats["fill_pairs_leaf"] == 0
+    assert h.stats["near_pairs_leaf"] == len(h.st.offsets[-1]) - 1       # diagonal blocks only
+    assert all(len(set(c)) == 1 for c in h.st.colors)
+    A = dense.kernel_matrix(W.TRIDIAG_TEST, (0, 0, 0, 0), h.X)
+    assert np.linalg.norm(A - h2.dense_approximation(h)) < 1e-12 * np.linalg.norm(A)
+    ev = toeplitz_eigs(n)
+    for mu in gaps_shifts(ev, 3):
+        assert h2.h2_inertia(h, mu)[0] == int(np.sum(ev < mu))
+
+
+def test_weak_min_matrix_exact():
+    n = 128
+    h = h2.construct(W.line_points(n), W.MIN_TEST, (0, 0, 0, 0), 16, 8, 1.0, rule=h2.ADM_WEAK)
+    A = dense.kernel_matrix(W.MIN_TEST, (0, 0, 0, 0), h.X)
+    assert np.linalg.norm(A - h2.dense_approximation(h)) < 1e-12 * np.linalg.norm(A)
+    ev = min_eigs(n)
+    for mu in gaps_shifts(ev, 4):
+        assert h2.h2_inertia(h, mu)[0] == int(np.sum(ev < mu))
+
+
+def test_weak_unit_circle_counts():
+    """The paper's synthetic Laplace matrix (points on the unit circle) in HSS
+    form: rank 40 reproduces the dense counts at midpoints between eigenvalues."""
+    X = W.unit_circle(256, 5)
+    kp = (1e-3, 0, 0, 0)
+    h = h2.construct(X, W.LAPLACE_EPS, kp, 32, 40, 1.0, rule=h2.ADM_WEAK)
+    A = dense.kernel_matrix(W.LAPLACE_EPS, kp, h.X)
+    err = np.linalg.norm(A - h2.dense_approximation(h), 2) / np.linalg.norm(A, 2)
+    assert err < 1e-6, err
+    ev = dense.eigenvalues(A)
+    shifts = gaps_shifts(ev, 17)
+    gap = np.array([np.abs(ev - mu).min() for mu in shifts])
+    for mu, g in zip(shifts, gap):
+        if g > 1e-3:
+            assert h2.h2_inertia(h, mu)[0] == int(np.sum(ev < mu))

@@ -69,6 +69,14 @@ def cylinder_lattice(n: int, seed: int, radius: float = 5.0, spacing: float = 0.
     return pts + jitter * gaussian(seed, 3 * n).reshape(n, 3)
 
 
+def unit_circle(n: int, seed: int) -> np.ndarray:
+    """n points uniformly distributed on the circumference of the unit circle
+    (angles 2 pi U), n x 2: the synthetic Laplace workload of the paper's
+    Sec. 5.1."""
+    t = 2.0 * math.pi * uniform(seed, n)
+    return np.stack([np.cos(t), np.sin(t)], axis=1)
+
+
 def line_points(n: int) -> np.ndarray:
     """Points 1, 2, ..., n on a line (n×1): the closed-form test matrices."""
     return np.arange(1, n + 1, dtype=np.float64).reshape(n, 1)
