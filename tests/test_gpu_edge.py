@@ -48,6 +48,46 @@ def test_bench_launch_configuration_sampled_against_oracle(pkg):
     assert np.all(np.diff(got) >= 0)
 
 
+@pytest.mark.parametrize("prec", [2, 1])
+def test_bench_launch_configuration_other_precisions(pkg, prec):
+    """The bench also times FP64_TC and mixed 256-lane batches of the n = 1024
+    workload.  FP64_TC: sampled lanes equal the H^2 oracle's counts one by one.
+    Mixed: the lanes farther than Delta = 64 * 2^-24 ||A||_inf from the dense
+    spectrum (where a mixed count is exact, see h2_kth_eig) equal the dense
+    counts."""
+    X = W.uniform_cube(1024, 2, 1)
+    kp = (1e-3, 0, 0, 0)
+    M = pkg.H2Matrix(X, W.LAPLACE_EPS, kp, leaf=64, rank=16, max_lanes=256, precision=prec)
+    info = M.h2_info()
+    lo, hi = info["gershgorin_lo"], info["gershgorin_hi"]
+    u = W.uniform(7, 256)
+    shifts = lo + (hi - lo) * (np.arange(256) + u) / 256
+    import torch
+    d_sh = torch.tensor(shifts, dtype=torch.float64, device="cuda")
+    d_c = torch.zeros(256, dtype=torch.int64, device="cuda")
+    d_mp = torch.zeros(256, dtype=torch.float64, device="cuda")
+    M.h2_inertia_device(d_sh, 256, d_c, d_mp)       # the bench's path (no FP64 re-run)
+    torch.cuda.synchronize()
+    got, mp = d_c.cpu().numpy(), d_mp.cpu().numpy()
+    if prec == 2:
+        ref = oh2.construct(X, W.LAPLACE_EPS, kp, 64, 16, 1.0)
+        checked = 0
+        for i in range(0, 256, 37):
+            want, wmp, _ = oh2.h2_inertia(ref, shifts[i])
+            if min(mp[i], wmp) > 1e-10 * ref.scale:
+                assert got[i] == want, (i, shifts[i])
+                checked += 1
+        assert checked >= 5
+    else:
+        A = dense.kernel_matrix(W.LAPLACE_EPS, kp, X)
+        want, ev = _dense_counts(A, shifts)
+        delta = 64 * 2.0 ** -24 * info["norm_inf"]
+        far = np.abs(shifts[:, None] - ev[None, :]).min(axis=1) > delta
+        assert far.sum() >= 64
+        assert np.array_equal(got[far], want[far])
+    assert M.h2_status()[0] == 0
+
+
 @pytest.mark.parametrize("n", [1, 2, 3])
 def test_tiny_matrices(pkg, n):
     X = W.uniform_cube(n, 2, 70 + n)
