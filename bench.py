@@ -294,7 +294,8 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
     X = _points(WORKLOAD)
     t0 = time.time()
     M = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
-                     eta=WORKLOAD["eta"], max_lanes=lanes, stream=stream.cuda_stream, precision=args.precision)
+                     eta=WORKLOAD["eta"], max_lanes=lanes, stream=stream.cuda_stream, precision=args.precision,
+                     autotune=1)
     torch.cuda.synchronize()
     build_s = time.time() - t0
     info = M.h2_info()
@@ -520,6 +521,7 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
             "config": {"workload": WORKLOAD["name"], "n": WORKLOAD["n"], "leaf": WORKLOAD["leaf"],
                        "rank": WORKLOAD["rank"], "eta": WORKLOAD["eta"], "admissibility": "box",
                        "shifts_per_step": lanes, "parallelism": "replica per GPU",
+                       "autotuned_levels": [list(M.h2_autotune_choice(l)) for l in range(info["levels"])],
                        "l2": "per-step working set %.0f MB > 129 MB L2" % ws_mb},
             "e2e": {"value": e2e_value, "unit": "shifts/s", "h2d_bytes_per_step": 8 * lanes,
                     "d2h_bytes_per_step": 8 * lanes, "counts_match_device_path": same},
