@@ -171,6 +171,24 @@ int h2_inertia_device(h2_handle h, const double* d_shifts, int64_t ns, int64_t* 
  */
 int h2_autotune_choice(h2_handle h, int level, int* out);
 
+/*
+ * h2_plan_summary -- the cluster tree and block structure that h2_build would
+ * use for these points (binary tree, top-down block tree under the given
+ * admissibility, fill-in closure, distance-2 colouring); host only, no device
+ * is touched.  For tests and inspection.
+ *   points    : host, n x d row-major FP64.
+ *   perm      : host, n int64 (tree position -> input index), or NULL.
+ *   levels    : receives L + 1 (levels 0 = root .. L = leaves).
+ *   per_level : host, 5 * 64 int64, or NULL; for level l: [5l] clusters,
+ *               [5l+1] near pairs, [5l+2] fill pairs, [5l+3] far pairs
+ *               (ordered pairs, the diagonal included in near), [5l+4] colours.
+ *   colours   : host, one int per cluster of every level (level-major, root
+ *               first), or NULL.  The caller sizes it from a first call.
+ * Errors: H2_ERR_INVALID_ARG (as h2_build; more than 64 levels).
+ */
+int h2_plan_summary(const double* points, int64_t n, int d, int leaf, double eta, int rule,
+                    int64_t* perm, int* levels, int64_t* per_level, int* colours);
+
 /* ---- batches over several matrices (one launch per level and colour) ---- */
 typedef struct h2_group_set* h2_group;
 

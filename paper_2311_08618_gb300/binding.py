@@ -21,7 +21,7 @@ EXPORTED_SYMBOLS = ["h2_default_options", "h2_build", "h2_destroy", "h2_last_err
                     "h2_inertia_device", "h2_kth_eig", "h2_info", "h2_tree_perm", "h2_level_ranks",
                     "h2_profile_batch", "h2_dense_inertia_noalloc", "h2_status", "h2_heartbeat",
                     "h2_group_create", "h2_group_inertia_device", "h2_group_launches", "h2_group_destroy",
-                    "h2_autotune_choice"]
+                    "h2_autotune_choice", "h2_plan_summary"]
 KIND_NAMES = ["init", "recomp", "rotate", "ldl", "trsm", "schur", "merge", "other"]
 
 
@@ -97,6 +97,8 @@ def lib():
         L.h2_group_destroy.restype = None
         L.h2_autotune_choice.argtypes = [P, C.c_int, P]
         L.h2_autotune_choice.restype = C.c_int
+        L.h2_plan_summary.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_int, P, P, P, P]
+        L.h2_plan_summary.restype = C.c_int
         for f in ("h2_build", "h2_inertia", "h2_inertia_device", "h2_kth_eig", "h2_info",
                   "h2_tree_perm", "h2_level_ranks", "h2_profile_batch"):
             getattr(L, f).restype = C.c_int
@@ -246,3 +248,28 @@ class H2Group:
         n = np.ascontiguousarray(ns, dtype=np.int32).ravel()
         _check(lib().h2_group_inertia_device(self._g, _ptr(d_shifts), n.ctypes.data_as(C.c_void_p),
                                              _ptr(d_counts), _ptr(d_minpiv)))
+
+
+def plan_summary(points, leaf: int, eta: float = 1.0, rule: int = 0):
+    """h2_plan_summary: (perm, per-level [clusters, near, fill, far, colours],
+    per-level colour arrays) of the structure h2_build would use (host only)."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    if pts.ndim == 1:
+        pts = pts.reshape(-1, 1)
+    n, d = pts.shape
+    perm = np.zeros(n, dtype=np.int64)
+    lv = C.c_int(0)
+    per = np.zeros(5 * 64, dtype=np.int64)
+    _check(lib().h2_plan_summary(pts.ctypes.data_as(C.c_void_p), n, d, leaf, float(eta), rule,
+                                 perm.ctypes.data_as(C.c_void_p), C.byref(lv), per.ctypes.data_as(C.c_void_p),
+                                 None))
+    L1 = lv.value
+    per = per[:5 * L1].reshape(L1, 5)
+    cols = np.zeros(int(per[:, 0].sum()), dtype=np.int32)
+    _check(lib().h2_plan_summary(pts.ctypes.data_as(C.c_void_p), n, d, leaf, float(eta), rule,
+                                 None, C.byref(lv), None, cols.ctypes.data_as(C.c_void_p)))
+    out, pos = [], 0
+    for l in range(L1):
+        out.append(cols[pos:pos + per[l, 0]])
+        pos += per[l, 0]
+    return perm, per, out

@@ -144,6 +144,43 @@ int h2_autotune_choice(h2_handle h, int level, int* out) {
     return tune_choice(h, level, out);
 }
 
+int h2_plan_summary(const double* points, int64_t n, int d, int leaf, double eta, int rule,
+                    int64_t* perm, int* levels, int64_t* per_level, int* colours) {
+    g_last_error.clear();
+    if (!points || !levels || n < 1 || d < 1 || d > 3 || leaf < 2 || !(eta > 0.0) ||
+        (rule != H2_ADM_BOX && rule != H2_ADM_CENTER && rule != H2_ADM_WEAK)) {
+        set_error("h2_plan_summary: bad arguments");
+        return H2_ERR_INVALID_ARG;
+    }
+    Plan P = make_plan(points, n, d, leaf, eta, rule);
+    if (P.L + 1 > 64) { set_error("h2_plan_summary: more than 64 levels"); return H2_ERR_INVALID_ARG; }
+    *levels = P.L + 1;
+    if (perm)
+        for (int64_t i = 0; i < n; ++i) perm[i] = P.perm[i];
+    int64_t pos = 0;
+    for (int l = 0; l <= P.L; ++l) {
+        const LevelPlan& lp = P.lev[l];
+        if (per_level) {
+            int64_t nn = 0, nf = 0, nfar = 0;
+            for (int c = 0; c < lp.nc; ++c)
+                for (int e = 0; e < lp.nc; ++e) {
+                    nn += lp.is_near(c, e);
+                    nf += lp.is_fill(c, e);
+                    nfar += lp.is_far(c, e);
+                }
+            per_level[5 * l] = lp.nc;
+            per_level[5 * l + 1] = nn;
+            per_level[5 * l + 2] = nf;
+            per_level[5 * l + 3] = nfar;
+            per_level[5 * l + 4] = (int64_t)lp.color_lists.size();
+        }
+        if (colours)
+            for (int c = 0; c < lp.nc; ++c) colours[pos + c] = lp.color[c];
+        pos += lp.nc;
+    }
+    return H2_OK;
+}
+
 int h2_group_create(const h2_handle* hs, int nh, h2_group* out) {
     g_last_error.clear();
     if (!hs || !out || nh < 1) { set_error("h2_group_create: bad arguments"); return H2_ERR_INVALID_ARG; }
