@@ -92,6 +92,7 @@ struct ScratchLayout {
     // and Y (k padded with zero digits to dk, a multiple of 32) and the
     // largest biased exponent of every row [target][row]
     size_t wd, yd, we, ye;
+    size_t vd, ve;     // FP64_TC: digit planes of V^T [digit][row][dk] and row exponents
     int dk;
     size_t total;
 };
@@ -117,6 +118,8 @@ static ScratchLayout scratch_layout(int D, int nfill_max, int ntarg_max, bool di
         s.yd = o; o += plane; al();
         s.we = o; o += ((size_t)ntarg_max * D + 1) / 2; al();
         s.ye = o; o += ((size_t)ntarg_max * D + 1) / 2; al();
+        s.vd = o; o += (size_t)8 * D * s.dk / 4; al();
+        s.ve = o; o += ((size_t)D + 1) / 2; al();
     }
     s.total = o;
     return s;
@@ -197,6 +200,130 @@ __device__ __noinline__ void report_bad(int* err, int kernel, int a, int b, int 
 // [4] recompression ran, [8 + ti] live rows of target ti
 constexpr int HDR_ROWS = 8;
 
+// Digits of the FP64_TC Schur products (see k_schur_oz).
+constexpr int OZP = 8;
+constexpr int OZK = 32;
+constexpr int OZLD = OZK + 8;   // BF16 row stride: fragment loads hit 32 distinct banks
+
+// biased exponent field of x (0 for zero and subnormals)
+__device__ __forceinline__ int oz_expo(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+// the 8 BF16 digits of x for a row whose largest biased exponent is emax
+__device__ __forceinline__ void oz_digits(double x, int emax, uint32_t (&d)[OZP]) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    unsigned long long F = 0;
+    if (ex != 0) {
+        const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
+        const int sh = ex - emax + 3;            // F = |x| 2^(56 - e) = M 2^sh < 2^56
+        F = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> -sh) : 0ull);
+    }
+    const uint32_t sg = (uint32_t)(b >> 48) & 0x8000u;
+#pragma unroll
+    for (int p = 0; p < OZP; ++p) {
+        const uint32_t v = (uint32_t)(F >> (49 - 7 * p)) & 127u;
+        const float f = __uint_as_float(0x4B000000u | v) - 8388608.0f;   // (float)v, exact
+        d[p] = (__float_as_uint(f) >> 16) | (v ? sg : 0u);              // BF16 bits, exact
+    }
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// an integer-valued float below 2^22 in magnitude, as int (exact)
+__device__ __forceinline__ long long oz_int(float v) {
+    return (long long)(__float_as_int(v + 12582912.0f) - 0x4B400000);
+}
+
+// One warp's 16 x 8 output piece (rows 16 mi.., columns 8 ni..) over kc <= OZK
+// values of k: the 36 digit-pair products, folded exactly into hi / lo.
+// Digit p of row r, column k of an operand sits at X + p * xp + r * xl + k.
+__device__ __forceinline__ void oz_warp_chunk(const uint16_t* A, int ap, int al, const uint16_t* B, int bp, int bl,
+                                              int mi, int ni, int kc, long long (&hi)[4], long long (&lo)[4]) {
+    const int l = threadIdx.x % 32, gid = l / 4, tig = l % 4;
+    float acc[OZP][4];
+#pragma unroll
+    for (int t = 0; t < OZP; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+    for (int s0 = 0; s0 < kc; s0 += 16) {
+        uint32_t b[OZP][2];
+#pragma unroll
+        for (int q = 0; q < OZP; ++q) {
+            const uint16_t* bq = B + q * bp + (8 * ni + gid) * bl + s0 + 2 * tig;
+            b[q][0] = *reinterpret_cast<const uint32_t*>(bq);
+            b[q][1] = *reinterpret_cast<const uint32_t*>(bq + 8);
+        }
+#pragma unroll
+        for (int p = 0; p < OZP; ++p) {
+            const uint16_t* ap0 = A + p * ap + (16 * mi + gid) * al + s0 + 2 * tig;
+            uint32_t a[4];
+            a[0] = *reinterpret_cast<const uint32_t*>(ap0);
+            a[1] = *reinterpret_cast<const uint32_t*>(ap0 + 8 * al);
+            a[2] = *reinterpret_cast<const uint32_t*>(ap0 + 8);
+            a[3] = *reinterpret_cast<const uint32_t*>(ap0 + 8 * al + 8);
+#pragma unroll
+            for (int q = 0; q < OZP - p; ++q) mma_bf16(acc[p + q], a, b[q][0], b[q][1]);
+        }
+    }
+    // level t = p + q + 2: hi gets t = 2..5, lo gets t = 6..9 (exact)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        long long h = oz_int(acc[0][c]);
+        h = h * 128 + oz_int(acc[1][c]);
+        h = h * 128 + oz_int(acc[2][c]);
+        h = h * 128 + oz_int(acc[3][c]);
+        long long g = oz_int(acc[4][c]);
+        g = g * 128 + oz_int(acc[5][c]);
+        g = g * 128 + oz_int(acc[6][c]);
+        g = g * 128 + oz_int(acc[7][c]);
+        hi[c] += h;
+        lo[c] += g;
+    }
+}
+
+// the FP64 value of a folded product: (hi 2^-35 + lo 2^-63) 2^(e_row + e_col),
+// from the rows' largest biased exponents (one rounding)
+__device__ __forceinline__ double oz_value(long long hi, long long lo, int erow, int ecol) {
+    const int e = (erow - 1022) + (ecol - 1022) - 35;
+    const double v = fma((double)lo, 0x1p-28, (double)hi);   // exact operands, one rounding
+    const double sc = (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+    return v * sc;
+}
+
+// digit planes (row-scaled) of the R x R operand X^T for X = V: row i of
+// X^T is column i of V (leading dimension ldv), written as [p][i][dk] with
+// zero digits for k in [R, round32(R)); ve[i] = the row's largest exponent.
+// All threads of the CTA call it.
+__device__ void oz_planes_of_transpose(const double* V, int ldv, int R, int D, int dk, uint16_t* vd, int* ve) {
+    const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+    for (int i = w; i < R; i += blockDim.x / 32) {
+        int e = 0;
+        for (int k = l; k < R; k += 32) e = max(e, oz_expo(V[(size_t)k * ldv + i]));
+        for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+        if (l == 0) ve[i] = e;
+    }
+    __syncthreads();
+    const int npair = (R + 31) / 32 * 16;
+    for (int e = threadIdx.x; e < R * npair; e += blockDim.x) {
+        const int i = e / npair, k = 2 * (e % npair);
+        const double x0 = k < R ? V[(size_t)k * ldv + i] : 0.0;
+        const double x1 = k + 1 < R ? V[(size_t)(k + 1) * ldv + i] : 0.0;
+        uint32_t d0[OZP], d1[OZP];
+        oz_digits(x0, ve[i], d0);
+        oz_digits(x1, ve[i], d1);
+#pragma unroll
+        for (int p = 0; p < OZP; ++p)
+            *reinterpret_cast<uint32_t*>(&vd[((size_t)p * D + i) * dk + k]) = d0[p] | (d1[p] << 16);
+    }
+    __syncthreads();
+}
+
 // Multi-matrix (grouped) launches.  A grouped launch runs one kernel over the
 // work of several handles: item m (a handle's level and colour) owns the
 // blockIdx.x range [off[m], off[m+1]) and its own argument struct; flag[m]
@@ -273,6 +400,9 @@ __device__ __forceinline__ void k_recomp_body(const FactorArgs& A, const int bx,
         int capt = max(0, min(A.fill_cap, m) - r0);
         t = cta_pivqr<NT>(Z, wz, R, wz, A.tol, capt, Vr, D, red, redi, &s_bad);
         if (t > 0) cta_form_q<NT>(Vq, D, R, Vr, D, t);
+        if (t > 0 && A.lay.dk > 0)        // FP64_TC: digit planes of Vq^T for the rotation
+            oz_planes_of_transpose(Vq, D, R, D, A.lay.dk, reinterpret_cast<uint16_t*>(scr + A.lay.vd),
+                                   reinterpret_cast<int*>(scr + A.lay.ve));
         if (threadIdx.x == 0)
             add_stats(A.stats, H2_KIND_RECOMP, 4.0 * R * (double)wz * t + 4.0 * (double)R * R * t,
                       8.0 * 2.0 * R * (double)wz);
@@ -474,6 +604,9 @@ __device__ __forceinline__ void k_recomp_cluster_body(const FactorArgs& A, const
         t = cluster_pivqr(cl, g, Z, wz, R, wz, A.tol, capt, Vr, D, sv, red, redi, xs, &s_bad);
         if (g == 0) {
             if (t > 0) cta_form_q<NT>(Vq, D, R, Vr, D, t);
+            if (t > 0 && A.lay.dk > 0)
+                oz_planes_of_transpose(Vq, D, R, D, A.lay.dk, reinterpret_cast<uint16_t*>(scr + A.lay.vd),
+                                       reinterpret_cast<int*>(scr + A.lay.ve));
             if (threadIdx.x == 0)
                 add_stats(A.stats, H2_KIND_RECOMP, 4.0 * R * (double)wz * t + 4.0 * (double)R * R * t,
                           8.0 * 2.0 * R * (double)wz);
@@ -752,6 +885,156 @@ __global__ void __launch_bounds__(NT) k_rotate_fp64_g(GroupArgs<FactorArgs> G) {
     k_rotate_fp64_body(G.args[m], blockIdx.x - G.off[m], blockIdx.y);
 }
 
+// FP64_TC rotation: the same products as k_rotate_fp64 (rows r0.. of the
+// block become V^T old; for the diagonal block, columns r0.. become old V)
+// from exact 7-bit digits on the tensor cores (see k_schur_oz).  V^T's digit
+// planes come from the recompression kernel; the block's digits are taken for
+// 32 columns (rows) at a time, all of them before any output of that chunk is
+// written, so the update stays in place.
+__host__ __device__ constexpr int oz_rpad(int D) { return (D + 31) / 32 * 32; }
+__host__ __device__ constexpr size_t rotate_oz_smem(int D) {
+    return (size_t)OZP * TS * (oz_rpad(D) + 8) * 2 + (size_t)OZP * TS * OZLD * 2 + TS * sizeof(int);
+}
+
+__device__ __forceinline__ void k_rotate_oz_body(const FactorArgs& A, const int bx, const int by) {
+    HbScope hb_(2);
+    const int ci = bx / A.nrow_max, b = bx % A.nrow_max, lane = by;
+    if (lane >= *A.active || b >= A.nrow[ci]) return;
+    extern __shared__ __align__(16) unsigned char rz_smem[];
+    const int D = A.D, LN = A.lanes;
+    const int p = A.cl[ci];
+    const double* scr = A.scratch + ((size_t)ci * LN + lane) * A.lay.total;
+    const int* hdr = (const int*)(scr + A.lay.hdr);
+    if (!hdr[4]) return;
+    const int r0 = hdr[2], t = hdr[3];
+    const int m = A.dim[p * LN + lane];
+    const int R = m - r0;
+    const int x = A.rowblk_other[ci * A.nrow_max + b];
+    const int tr = A.rowblk_trans[ci * A.nrow_max + b];
+    double* B = slot_ptr(A.slots, A.rowblk[ci * A.nrow_max + b], LN, lane, D);
+    {
+        const int dxl = live_rows(A, x, lane), dqa = A.dim[x * LN + lane];
+        if (m < 0 || m > D || r0 < 0 || r0 > m || t < 0 || t > R || dxl < 0 || dxl > D || dqa < 0 || dqa > D) {
+            if (threadIdx.x == 0) report_bad(A.err, 2, m, r0, t, dqa);
+            return;
+        }
+    }
+    double fl = 0.0;
+    if (t > 0) {
+        const int dk = A.lay.dk, Rp32 = oz_rpad(R), LA = oz_rpad(D) + 8;
+        const uint16_t* vd = reinterpret_cast<const uint16_t*>(scr + A.lay.vd);
+        const int* ve = reinterpret_cast<const int*>(scr + A.lay.ve);
+        uint16_t* sAll = reinterpret_cast<uint16_t*>(rz_smem);              // [OZP][TS][LA]: the block's digits
+        uint16_t* sCh = sAll + (size_t)OZP * TS * LA;                        // [OZP][TS][OZLD]: V^T digits
+        int* sExp = reinterpret_cast<int*>(sCh + (size_t)OZP * TS * OZLD);   // [TS]
+        const int w = threadIdx.x / 32, l = threadIdx.x % 32, gid = l / 4, tig = l % 4;
+        const int mi = w / 4, ni = w % 4;
+        // copy rows v0.. of V^T's planes, k0.. (32 x 32) into sCh
+        auto copy_vt = [&](int v0, int nrow, int k0) {
+            for (int e = threadIdx.x; e < OZP * TS * 4; e += NT) {
+                const int pp = e / (TS * 4), r = (e / 4) % TS, c = e % 4;
+                int4 v = make_int4(0, 0, 0, 0);
+                if (r < nrow) v = *reinterpret_cast<const int4*>(&vd[((size_t)pp * D + v0 + r) * dk + k0 + 8 * c]);
+                *reinterpret_cast<int4*>(&sCh[((size_t)pp * TS + r) * OZLD + 8 * c]) = v;
+            }
+        };
+        // digits of 32 vectors of R values (vector jj, entry k) = get(jj, k), with
+        // each vector's largest exponent, into sAll / sExp
+        auto take = [&](int nvec, auto get) {
+            for (int jj = w; jj < TS; jj += NT / 32) {
+                int e = 0;
+                if (jj < nvec)
+                    for (int k = l; k < R; k += 32) e = max(e, oz_expo(get(jj, k)));
+                for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+                if (l == 0) sExp[jj] = e;
+            }
+            __syncthreads();
+            const int npair = Rp32 / 2;
+            for (int e = threadIdx.x; e < TS * npair; e += NT) {
+                const int jj = e / npair, k = 2 * (e % npair);
+                const double x0 = (jj < nvec && k < R) ? get(jj, k) : 0.0;
+                const double x1 = (jj < nvec && k + 1 < R) ? get(jj, k + 1) : 0.0;
+                uint32_t d0[OZP], d1[OZP];
+                oz_digits(x0, sExp[jj], d0);
+                oz_digits(x1, sExp[jj], d1);
+#pragma unroll
+                for (int pp = 0; pp < OZP; ++pp)
+                    *reinterpret_cast<uint32_t*>(&sAll[((size_t)pp * TS + jj) * LA + k]) = d0[pp] | (d1[pp] << 16);
+            }
+            __syncthreads();
+        };
+        // row side: rows r0 + i (i < R), columns j0.. of the dx live columns of x
+        const int dx = (x == p) ? m : live_rows(A, x, lane);
+        for (int j0 = 0; j0 < dx; j0 += TS) {
+            const int nj = min(TS, dx - j0);
+            take(nj, [&](int jj, int k) { return belem(B, D, tr, r0 + k, j0 + jj); });
+            for (int i0 = 0; i0 < R; i0 += TS) {
+                const int nr = min(TS, R - i0);
+                const bool act = 16 * mi < nr && 8 * ni < nj;
+                long long hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+                for (int k0 = 0; k0 < R; k0 += OZK) {
+                    copy_vt(i0, nr, k0);
+                    __syncthreads();
+                    if (act)
+                        oz_warp_chunk(sCh, TS * OZLD, OZLD, sAll + k0, TS * LA, LA, mi, ni, min(OZK, R - k0), hi, lo);
+                    __syncthreads();
+                }
+                if (act)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int r = 16 * mi + gid + (c >= 2 ? 8 : 0), q = 8 * ni + 2 * tig + (c & 1);
+                        if (r < nr && q < nj)
+                            belem(B, D, tr, r0 + i0 + r, j0 + q) = oz_value(hi[c], lo[c], ve[i0 + r], sExp[q]);
+                    }
+            }
+            __syncthreads();
+        }
+        fl += 2.0 * R * (double)R * dx;
+        if (x == p) {   // column side: columns r0.. of every row, new = old V
+            for (int i0 = 0; i0 < m; i0 += TS) {
+                const int nr = min(TS, m - i0);
+                take(nr, [&](int ii, int k) { return B[(size_t)(i0 + ii) * D + r0 + k]; });
+                for (int j0 = 0; j0 < R; j0 += TS) {
+                    const int nc = min(TS, R - j0);
+                    const bool act = 16 * mi < nr && 8 * ni < nc;
+                    long long hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+                    for (int k0 = 0; k0 < R; k0 += OZK) {
+                        copy_vt(j0, nc, k0);
+                        __syncthreads();
+                        if (act)
+                            oz_warp_chunk(sAll + k0, TS * LA, LA, sCh, TS * OZLD, OZLD, mi, ni, min(OZK, R - k0), hi,
+                                          lo);
+                        __syncthreads();
+                    }
+                    if (act)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int r = 16 * mi + gid + (c >= 2 ? 8 : 0), q = 8 * ni + 2 * tig + (c & 1);
+                            if (r < nr && q < nc)
+                                B[(size_t)(i0 + r) * D + r0 + j0 + q] = oz_value(hi[c], lo[c], sExp[r], ve[j0 + q]);
+                        }
+                }
+                __syncthreads();
+            }
+            fl += 2.0 * m * (double)R * R;
+        }
+    }
+    if (A.rowblk_fill[ci * A.nrow_max + b]) {   // drop the remaining redundant rows
+        const int dq = A.dim[x * LN + lane];
+        const int rows = m - (r0 + t);
+        for (int e = threadIdx.x; e < rows * dq; e += NT) {
+            int i = e / dq, j = e % dq;
+            belem(B, D, tr, r0 + t + i, j) = 0.0;
+        }
+    }
+    if (threadIdx.x == 0 && fl > 0.0) add_stats(A.stats, H2_KIND_ROTATE, fl, 8.0 * fl / R);
+}
+__global__ void __launch_bounds__(NT) k_rotate_oz(FactorArgs A) { k_rotate_oz_body(A, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(NT) k_rotate_oz_g(GroupArgs<FactorArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_rotate_oz_body(G.args[m], blockIdx.x - G.off[m], blockIdx.y);
+}
+
 // ---- (iii) Bunch-Kaufman LDL^T of S_pp^RR (Eq. blr2-diag-ldl) and its
 // negative-pivot count: one CTA per (cluster, lane)
 template <int NTH>
@@ -884,47 +1167,6 @@ __global__ void __launch_bounds__(32 * LW) k_ldl_warp_g(GroupArgs<FactorArgs> G)
     k_ldl_warp_body(G.args[m], blockIdx.x - G.off[m]);
 }
 
-// Digits of the FP64_TC Schur products (see k_schur_oz).
-constexpr int OZP = 8;
-constexpr int OZK = 32;
-constexpr int OZLD = OZK + 8;   // BF16 row stride: fragment loads hit 32 distinct banks
-
-// biased exponent field of x (0 for zero and subnormals)
-__device__ __forceinline__ int oz_expo(double x) {
-    return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
-}
-
-// the 8 BF16 digits of x for a row whose largest biased exponent is emax
-__device__ __forceinline__ void oz_digits(double x, int emax, uint32_t (&d)[OZP]) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int ex = (int)((b >> 52) & 0x7ff);
-    unsigned long long F = 0;
-    if (ex != 0) {
-        const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
-        const int sh = ex - emax + 3;            // F = |x| 2^(56 - e) = M 2^sh < 2^56
-        F = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> -sh) : 0ull);
-    }
-    const uint32_t sg = (uint32_t)(b >> 48) & 0x8000u;
-#pragma unroll
-    for (int p = 0; p < OZP; ++p) {
-        const uint32_t v = (uint32_t)(F >> (49 - 7 * p)) & 127u;
-        const float f = __uint_as_float(0x4B000000u | v) - 8388608.0f;   // (float)v, exact
-        d[p] = (__float_as_uint(f) >> 16) | (v ? sg : 0u);              // BF16 bits, exact
-    }
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// an integer-valued float below 2^22 in magnitude, as int (exact)
-__device__ __forceinline__ long long oz_int(float v) {
-    return (long long)(__float_as_int(v + 12582912.0f) - 0x4B400000);
-}
 
 // ---- (iv) W_a = S_ap^{.R} P L^{-T}, Y_a = W_a D^{-1} (Eq. blr2-diag-elimination):
 // one CTA per (target, cluster, lane); column-blocked forward substitution
@@ -1314,43 +1556,7 @@ __device__ __forceinline__ void k_schur_oz_body(const SchurArgs& A, const int bx
             *reinterpret_cast<int4*>(op ? &sB[p][r][8 * c] : &sA[p][r][8 * c]) = v;
         }
         __syncthreads();
-        if (act) {
-            float acc[OZP][4];
-#pragma unroll
-            for (int t = 0; t < OZP; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
-            for (int s0 = 0; s0 < kc; s0 += 16) {
-                uint32_t b[OZP][2];
-#pragma unroll
-                for (int q = 0; q < OZP; ++q) {
-                    b[q][0] = *reinterpret_cast<const uint32_t*>(&sB[q][8 * ni + gid][s0 + 2 * tig]);
-                    b[q][1] = *reinterpret_cast<const uint32_t*>(&sB[q][8 * ni + gid][s0 + 2 * tig + 8]);
-                }
-#pragma unroll
-                for (int p = 0; p < OZP; ++p) {
-                    uint32_t a[4];
-                    a[0] = *reinterpret_cast<const uint32_t*>(&sA[p][16 * mi + gid][s0 + 2 * tig]);
-                    a[1] = *reinterpret_cast<const uint32_t*>(&sA[p][16 * mi + gid + 8][s0 + 2 * tig]);
-                    a[2] = *reinterpret_cast<const uint32_t*>(&sA[p][16 * mi + gid][s0 + 2 * tig + 8]);
-                    a[3] = *reinterpret_cast<const uint32_t*>(&sA[p][16 * mi + gid + 8][s0 + 2 * tig + 8]);
-#pragma unroll
-                    for (int q = 0; q < OZP - p; ++q) mma_bf16(acc[p + q], a, b[q][0], b[q][1]);
-                }
-            }
-            // level t = p + q + 2: hi gets t = 2..5, lo gets t = 6..9 (exact)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                long long h = oz_int(acc[0][c]);
-                h = h * 128 + oz_int(acc[1][c]);
-                h = h * 128 + oz_int(acc[2][c]);
-                h = h * 128 + oz_int(acc[3][c]);
-                long long g = oz_int(acc[4][c]);
-                g = g * 128 + oz_int(acc[5][c]);
-                g = g * 128 + oz_int(acc[6][c]);
-                g = g * 128 + oz_int(acc[7][c]);
-                hi[c] += h;
-                lo[c] += g;
-            }
-        }
+        if (act) oz_warp_chunk(&sA[0][0][0], TS * OZLD, OZLD, &sB[0][0][0], TS * OZLD, OZLD, mi, ni, kc, hi, lo);
         __syncthreads();
     }
     if (!act) return;
@@ -1358,13 +1564,7 @@ __device__ __forceinline__ void k_schur_oz_body(const SchurArgs& A, const int bx
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const int r = 16 * mi + gid + (c >= 2 ? 8 : 0), q = 8 * ni + 2 * tig + (c & 1);
-        if (r < nr && q < nc) {
-            const int e = (we[i0 + r] - 1022) + (ye[j0 + q] - 1022) - 35;
-            const double v = fma((double)lo[c], 0x1p-28, (double)hi[c]);   // exact operands, one rounding
-            const double sc = (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52)
-                                                        : ldexp(1.0, e);
-            belem(B, D, P.trans, i0 + r, j0 + q) -= v * sc;
-        }
+        if (r < nr && q < nc) belem(B, D, P.trans, i0 + r, j0 + q) -= oz_value(hi[c], lo[c], we[i0 + r], ye[j0 + q]);
     }
 }
 __global__ void __launch_bounds__(NT, 3) k_schur_oz(SchurArgs A) { k_schur_oz_body(A, blockIdx.x, blockIdx.y); }
@@ -1831,6 +2031,7 @@ int alloc_workspace(h2_matrix* h, int lanes) {
         if ((rc = upload(&W.d_slot_of, D.slot_of)) || (rc = upload(&W.d_far_of, D.far_of))) return rc;
     }
     CK(cudaFuncSetAttribute(k_rotate_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_rotate_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     CK(cudaFuncSetAttribute(k_rotate<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     CK(cudaFuncSetAttribute(k_rotate<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     CK(cudaFuncSetAttribute(k_rotate<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
@@ -2001,7 +2202,10 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
                 q.op = OP_ROTATE;
                 q.kind = H2_KIND_ROTATE;
                 q.grid = dim3(C.ncl * C.nrow_max, LN);
-                if (!mixed) {
+                if (!mixed && h->opt.precision == H2_PREC_FP64_TC && rotate_oz_smem(Dm) <= kSmemMax) {
+                    q.variant = 2;
+                    q.smem = rotate_oz_smem(Dm);
+                } else if (!mixed) {
                     q.variant = 0;
                     q.smem = (size_t)Dm * RC * sizeof(double);
                 } else {
@@ -2109,6 +2313,7 @@ static void launch_single(const LaunchRec& r, cudaStream_t st) {
         case OP_RECOMP_CL: k_recomp_cluster<<<r.grid, NT, r.smem, st>>>(r.fa); break;
         case OP_ROTATE:
             if (r.variant == 0) k_rotate_fp64<<<r.grid, NT, r.smem, st>>>(r.fa);
+            else if (r.variant == 2) k_rotate_oz<<<r.grid, NT, r.smem, st>>>(r.fa);
             else if (r.variant == 8) k_rotate<float, 8><<<r.grid, NT, r.smem, st>>>(r.fa);
             else if (r.variant == 16) k_rotate<float, 16><<<r.grid, NT, r.smem, st>>>(r.fa);
             else k_rotate<float, 32><<<r.grid, NT, r.smem, st>>>(r.fa);
@@ -2277,6 +2482,7 @@ static void launch_grouped(const GLaunch& gl, cudaStream_t st) {
         case OP_RECOMP_CL: k_recomp_cluster_g<<<grid, NT, gl.smem, st>>>(F); break;
         case OP_ROTATE:
             if (gl.variant == 0) k_rotate_fp64_g<<<grid, NT, gl.smem, st>>>(F);
+            else if (gl.variant == 2) k_rotate_oz_g<<<grid, NT, gl.smem, st>>>(F);
             else if (gl.variant == 8) k_rotate_g<float, 8><<<grid, NT, gl.smem, st>>>(F);
             else if (gl.variant == 16) k_rotate_g<float, 16><<<grid, NT, gl.smem, st>>>(F);
             else k_rotate_g<float, 32><<<grid, NT, gl.smem, st>>>(F);
@@ -2325,6 +2531,7 @@ int group_create(h2_matrix* const* hs, int nh, h2_group_set** out) {
             return H2_ERR_INVALID_ARG;
         }
     CK(cudaFuncSetAttribute(k_rotate_fp64_g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_rotate_oz_g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     CK(cudaFuncSetAttribute(k_rotate_g<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     CK(cudaFuncSetAttribute(k_rotate_g<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     CK(cudaFuncSetAttribute(k_rotate_g<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
