@@ -65,6 +65,7 @@ static int upload(T** p, const std::vector<T>& v) {
 
 constexpr int NT = 256;
 constexpr int TS = 32;   // Schur tile
+constexpr int TSF = 64;  // Schur tile of the mixed (FP32) path
 
 // Diagnostic heartbeat (enabled by H2_HEARTBEAT=1): per kernel kind, CTAs
 // started, threads finished, and the block indices of the last CTA started,
@@ -168,6 +169,28 @@ __device__ __forceinline__ double* slot_ptr(double* slots, int s, int lanes, int
 // element (i, j) of block (x, y) stored as (x, y) (trans = 0) or as (y, x) (trans = 1)
 __device__ __forceinline__ double& belem(double* B, int D, int trans, int i, int j) {
     return trans ? B[(size_t)j * D + i] : B[(size_t)i * D + j];
+}
+
+// Symmetric Schur updates.  The update of a diagonal block, S_aa -= W_a Y_a^T
+// = W_a D^-1 W_a^T, is symmetric: only the tiles on and below the tile
+// diagonal are computed, and each lower tile also writes its transpose into
+// the skipped upper tile.  Live entries of an r x r block covered by those
+// tiles (ts x ts):
+__device__ __forceinline__ double lower_tile_entries(int r, int ts) {
+    double s = 0.0;
+    for (int i0 = 0; i0 < r; i0 += ts) s += (double)min(ts, r - i0) * min(r, i0 + ts);
+    return s;
+}
+
+// S(j0 + c, i0 + r) -= T[r][c] for r < nr, c < nc: the mirror of lower tile
+// (i0, j0) staged in shared memory (ld = leading dimension of T).  Threads
+// run along r, so the writes are coalesced.  All threads of the CTA call it.
+template <typename V>
+__device__ __forceinline__ void schur_mirror(double* B, int D, int trans, int i0, int j0, int nr, int nc,
+                                             const V* T, int ld, int rows_per_pass) {
+    const int r = threadIdx.x % rows_per_pass;
+    for (int c = threadIdx.x / rows_per_pass; c < nc; c += blockDim.x / rows_per_pass)
+        if (r < nr) belem(B, D, trans, j0 + c, i0 + r) -= (double)T[(size_t)r * ld + c];
 }
 
 // rows of cluster x still in the trailing matrix: all of them until x is
@@ -1203,7 +1226,8 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
         for (int tj = 0; tj <= ti; ++tj) {
             int b2 = A.targ[ci * A.ntarg_max + tj];
             double rb = (b2 == p) ? rk1 : live_rows(A, b2, lane);
-            fs += 2.0 * rows * rb * Rp;
+            const double ent = tj == ti ? lower_tile_entries(rows, sizeof(T) == 4 ? TSF : TS) : rows * rb;
+            fs += 2.0 * ent * Rp;
             bs += 8.0 * (rows * (double)Rp + rb * Rp + 2.0 * rows * rb);
         }
         add_stats(A.stats, H2_KIND_SCHUR, fs, bs);
@@ -1446,6 +1470,11 @@ __device__ __forceinline__ void k_schur_body(const SchurArgs& A, const int bx, c
     }
     const int i0 = (tile / A.tdim) * TS, j0 = (tile % A.tdim) * TS;
     if (i0 >= ra || j0 >= rb) return;
+    if (P.ta == P.tb && j0 > i0) return;           // written by the mirror of tile (j0, i0)
+    // kept in shared memory, not in a register through the k loop (the
+    // loop's first barrier publishes it)
+    __shared__ int s_mirror;
+    if (threadIdx.x == 0) s_mirror = P.ta == P.tb && j0 < i0;
     const T* W = reinterpret_cast<const T*>(scr + A.lay.w + (size_t)P.ta * D * D);
     const T* Y = reinterpret_cast<const T*>(scr + A.lay.y + (size_t)P.tb * D * D);
     // A warp owns the rows ty + 8u of the tile: rows past the block are not
@@ -1478,6 +1507,7 @@ __device__ __forceinline__ void k_schur_body(const SchurArgs& A, const int bx, c
         }
         __syncthreads();
     }
+    const bool mirror = s_mirror;
     double* B = slot_ptr(A.slots, P.slot, A.lanes, lane, D);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -1485,11 +1515,18 @@ __device__ __forceinline__ void k_schur_body(const SchurArgs& A, const int bx, c
         if (r < nrow && tx < ncol) {
             const int i = tp ? i0 + tx : i0 + r, j = tp ? j0 + r : j0 + tx;
             belem(B, D, P.trans, i, j) -= (double)acc[u];
+            if (mirror) sR[i - i0][j - j0] = acc[u];   // the k loop ended with a barrier
         }
     }
+    if (mirror) {
+        __syncthreads();
+        schur_mirror(B, D, P.trans, i0, j0, tp ? ncol : nrow, tp ? nrow : ncol, &sR[0][0], TS + 1, TS);
+    }
 }
+// 8 CTAs of 256 threads per SM (32 registers): the FP64 pipe stays fed from
+// shared memory at full occupancy
 template <typename T>
-__global__ void __launch_bounds__(NT) k_schur(SchurArgs A) { k_schur_body<T>(A, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(NT, 8) k_schur(SchurArgs A) { k_schur_body<T>(A, blockIdx.x, blockIdx.y); }
 template <typename T>
 __global__ void __launch_bounds__(NT) k_schur_g(GroupArgs<SchurArgs> G) {
     const int m = group_find(G.off, G.n, blockIdx.x);
@@ -1531,6 +1568,9 @@ __device__ __forceinline__ void k_schur_oz_body(const SchurArgs& A, const int bx
     }
     const int i0 = (tile / A.tdim) * TS, j0 = (tile % A.tdim) * TS;
     if (i0 >= ra || j0 >= rb) return;
+    const bool diag = P.ta == P.tb;
+    if (diag && j0 > i0) return;                   // written by the mirror of tile (j0, i0)
+    const bool mirror = diag && j0 < i0;
     const int dk = A.lay.dk;
     const uint16_t* wd = reinterpret_cast<const uint16_t*>(scr + A.lay.wd) + (size_t)P.ta * OZP * D * dk;
     const uint16_t* yd = reinterpret_cast<const uint16_t*>(scr + A.lay.yd) + (size_t)P.tb * OZP * D * dk;
@@ -1559,12 +1599,22 @@ __device__ __forceinline__ void k_schur_oz_body(const SchurArgs& A, const int bx
         if (act) oz_warp_chunk(&sA[0][0][0], TS * OZLD, OZLD, &sB[0][0][0], TS * OZLD, OZLD, mi, ni, kc, hi, lo);
         __syncthreads();
     }
-    if (!act) return;
     double* B = slot_ptr(A.slots, P.slot, A.lanes, lane, D);
+    double* sT = reinterpret_cast<double*>(&sA[0][0][0]);   // TS x (TS + 1), free after the k loop
+    if (act) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int r = 16 * mi + gid + (c >= 2 ? 8 : 0), q = 8 * ni + 2 * tig + (c & 1);
-        if (r < nr && q < nc) belem(B, D, P.trans, i0 + r, j0 + q) -= oz_value(hi[c], lo[c], we[i0 + r], ye[j0 + q]);
+        for (int c = 0; c < 4; ++c) {
+            const int r = 16 * mi + gid + (c >= 2 ? 8 : 0), q = 8 * ni + 2 * tig + (c & 1);
+            if (r < nr && q < nc) {
+                const double v = oz_value(hi[c], lo[c], we[i0 + r], ye[j0 + q]);
+                belem(B, D, P.trans, i0 + r, j0 + q) -= v;
+                if (mirror) sT[r * (TS + 1) + q] = v;
+            }
+        }
+    }
+    if (mirror) {
+        __syncthreads();
+        schur_mirror(B, D, P.trans, i0, j0, nr, nc, sT, TS + 1, TS);
     }
 }
 __global__ void __launch_bounds__(NT, 3) k_schur_oz(SchurArgs A) { k_schur_oz_body(A, blockIdx.x, blockIdx.y); }
@@ -1578,7 +1628,6 @@ __global__ void __launch_bounds__(NT, 3) k_schur_oz_g(GroupArgs<SchurArgs> G) {
 // Thread (tx, ty) owns rows ty + 16 i and columns tx + 16 j (i, j < 4): the W
 // reads are warp broadcasts, the Y reads hit 16 distinct banks, and the FP64
 // read-modify-write of S is coalesced along rows.
-constexpr int TSF = 64;
 __device__ __forceinline__ void k_schur_f32_body(const SchurArgs& A, const int bx, const int by) {
     HbScope hb_(5);
     const int lane = by;
@@ -1597,9 +1646,14 @@ __device__ __forceinline__ void k_schur_f32_body(const SchurArgs& A, const int b
     }
     const int i0 = (tile / A.tdim) * TSF, j0 = (tile % A.tdim) * TSF;
     if (i0 >= ra || j0 >= rb) return;
+    const bool diag = P.ta == P.tb;
+    if (diag && j0 > i0) return;                   // written by the mirror of tile (j0, i0)
+    const bool mirror = diag && j0 < i0;
     const float* W = reinterpret_cast<const float*>(scr + A.lay.w + (size_t)P.ta * D * D);
     const float* Y = reinterpret_cast<const float*>(scr + A.lay.y + (size_t)P.tb * D * D);
-    __shared__ float sW[TSF][33], sY[TSF][33];
+    __shared__ float sbuf[2 * TSF * 33];            // the operand tiles, then the mirror's staging
+    float(*sW)[33] = reinterpret_cast<float(*)[33]>(sbuf);
+    float(*sY)[33] = reinterpret_cast<float(*)[33]>(sbuf + TSF * 33);
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     float acc[4][4];
 #pragma unroll
@@ -1634,8 +1688,15 @@ __device__ __forceinline__ void k_schur_f32_body(const SchurArgs& A, const int b
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             int r = i0 + ty + 16 * i, c = j0 + tx + 16 * j;
-            if (r < ra && c < rb) belem(B, D, P.trans, r, c) -= (double)acc[i][j];
+            if (r < ra && c < rb) {
+                belem(B, D, P.trans, r, c) -= (double)acc[i][j];
+                if (mirror) sbuf[(ty + 16 * i) * (TSF + 1) + tx + 16 * j] = acc[i][j];
+            }
         }
+    if (mirror) {
+        __syncthreads();
+        schur_mirror(B, D, P.trans, i0, j0, min(TSF, ra - i0), min(TSF, rb - j0), sbuf, TSF + 1, TSF);
+    }
 }
 __global__ void __launch_bounds__(NT) k_schur_f32(SchurArgs A) { k_schur_f32_body(A, blockIdx.x, blockIdx.y); }
 __global__ void __launch_bounds__(NT) k_schur_f32_g(GroupArgs<SchurArgs> G) {
@@ -2095,8 +2156,6 @@ struct Profiler {
     void after() { cudaEventRecord(ev[used++], st); }
 };
 
-// enqueue one full factorization of the workspace's lanes on stream st;
-// returns the number of kernel launches
 // One launch of a batch, described before it is launched, so that a single
 // handle launches its records one by one and a group of handles merges the
 // records of equal key (step, colour, operation, variant) into one grouped
@@ -2337,6 +2396,8 @@ static void launch_single(const LaunchRec& r, cudaStream_t st) {
     }
 }
 
+// enqueue one full factorization of the workspace's lanes on stream st;
+// returns the number of kernel launches
 static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, int mixed) {
     int nl = 0;
     for (const LaunchRec& r : factor_records(h, mixed)) {
