@@ -1246,8 +1246,12 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
         const double* F = scr + A.lay.f;
         const int* perm = (const int*)(scr + A.lay.iperm);
         const int* piv = perm + D;
-        T* sLz = reinterpret_cast<T*>(sh);                       // Rp x Rp
-        T* sWm = sLz + (size_t)Rp * Rp;                          // rows x (Rp + 1)
+        // rows of L and of W padded to Rp + 1 values: the update loop reads
+        // L(j, k) for 8 consecutive j in one warp, which a stride of Rp (a
+        // multiple of 16 at these levels) would put in one bank
+        const int ldl = Rp + 1;
+        T* sLz = reinterpret_cast<T*>(sh);                       // Rp x (Rp + 1)
+        T* sWm = sLz + (size_t)Rp * ldl;                         // rows x (Rp + 1)
         T* sDg = sWm + (size_t)rows * (Rp + 1);
         T* sOd = sDg + Rp;
         int* sPerm = reinterpret_cast<int*>(sOd + Rp);
@@ -1255,7 +1259,7 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
         const int ldw = Rp + 1;
         for (int e = threadIdx.x; e < Rp * Rp; e += NT) {
             const int j = e / Rp, k = e % Rp;
-            sLz[e] = (k < j && !(piv[k] == 2 && j == k + 1)) ? (T)F[(size_t)j * D + k] : (T)0;
+            sLz[j * ldl + k] = (k < j && !(piv[k] == 2 && j == k + 1)) ? (T)F[(size_t)j * D + k] : (T)0;
         }
         for (int j = threadIdx.x; j < Rp; j += NT) {
             sDg[j] = (T)F[(size_t)j * D + j];
@@ -1265,7 +1269,8 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
         }
         __syncthreads();
         for (int e = threadIdx.x; e < rows * Rp; e += NT) {      // W = S_ap^{.R} P
-            const int i = e / Rp, j = e % Rp;
+            // consecutive threads read consecutive addresses of the stored block
+            const int i = tr ? e % rows : e / Rp, j = tr ? e / rows : e % Rp;
             sWm[i * ldw + j] = (T)(tr ? B[(size_t)(rk1 + sPerm[j]) * D + i] : B[(size_t)i * D + rk1 + sPerm[j]]);
         }
         __syncthreads();
@@ -1275,7 +1280,7 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
                 for (int e = threadIdx.x; e < rows * nb; e += NT) {
                     const int i = e / nb, j = jb + e % nb;
                     const T* wi = sWm + i * ldw;
-                    const T* lj = sLz + (size_t)j * Rp;
+                    const T* lj = sLz + (size_t)j * ldl;
                     T v = wi[j];
                     for (int k = 0; k < jb; ++k) v -= wi[k] * lj[k];
                     sWm[i * ldw + j] = v;
@@ -1285,7 +1290,7 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
             for (int i = threadIdx.x; i < rows; i += NT) {
                 T* wi = sWm + i * ldw;
                 for (int j = jb + 1; j < jb + nb; ++j) {
-                    const T* lj = sLz + (size_t)j * Rp;
+                    const T* lj = sLz + (size_t)j * ldl;
                     T v = wi[j];
                     for (int k = jb; k < j; ++k) v -= wi[k] * lj[k];
                     wi[j] = v;
@@ -1317,11 +1322,12 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
         const T* sL = nullptr;
         const int* sperm = perm;
         const int* spiv = piv;
+        const int ldl = Rp + 1;                                      // padded as in the path above
         if (use_smem) {
-            T* L2 = reinterpret_cast<T*>(sh);                        // Rp x Rp
-            int* p2 = reinterpret_cast<int*>(L2 + (size_t)Rp * Rp);
+            T* L2 = reinterpret_cast<T*>(sh);                        // Rp x (Rp + 1)
+            int* p2 = reinterpret_cast<int*>(L2 + (size_t)Rp * ldl);
             int* v2 = p2 + Rp;
-            for (int e = threadIdx.x; e < Rp * Rp; e += NT) L2[e] = (T)F[(size_t)(e / Rp) * D + e % Rp];
+            for (int e = threadIdx.x; e < Rp * Rp; e += NT) L2[(e / Rp) * ldl + e % Rp] = (T)F[(size_t)(e / Rp) * D + e % Rp];
             for (int e = threadIdx.x; e < Rp; e += NT) { p2[e] = perm[e]; v2[e] = piv[e]; }
             sL = L2;
             sperm = p2;
@@ -1329,7 +1335,7 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
         }
         __syncthreads();
         auto Fx = [&](int j, int k) -> T {  // entry (j, k) of the packed factor
-            return use_smem ? sL[(size_t)j * Rp + k] : (T)F[(size_t)j * D + k];
+            return use_smem ? sL[(size_t)j * ldl + k] : (T)F[(size_t)j * D + k];
         };
         auto Lx = [&](int j, int k) -> T {  // L(j, k), k < j, of the unit lower factor
             return (spiv[k] == 2 && j == k + 1) ? (T)0 : Fx(j, k);
@@ -2293,9 +2299,9 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
                 R.push_back(q);
             }
             {
-                const size_t sm_trsm = (size_t)Dm * Dm * sizeof(double) + 2 * (size_t)Dm * sizeof(int);
-                // flag 2: L, D and W staged (Rp^2 + rows (Rp + 1) + 2 Rp values, 2 Rp ints)
-                const size_t sm_full = ((size_t)Dm * Dm + (size_t)Dm * (Dm + 1) + 2 * (size_t)Dm) * sizeof(double) +
+                const size_t sm_trsm = (size_t)Dm * (Dm + 1) * sizeof(double) + 2 * (size_t)Dm * sizeof(int);
+                // flag 2: L, D and W staged (Rp (Rp + 1) + rows (Rp + 1) + 2 Rp values, 2 Rp ints)
+                const size_t sm_full = ((size_t)Dm * (Dm + 1) + (size_t)Dm * (Dm + 1) + 2 * (size_t)Dm) * sizeof(double) +
                                        2 * (size_t)Dm * sizeof(int);
                 LaunchRec q = r;
                 q.op = OP_TRSM;
