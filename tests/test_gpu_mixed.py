@@ -86,3 +86,23 @@ def test_mixed_guard_reruns_low_pivot_shifts(pkg):
     cf, mf = F.h2_inertia(shifts)
     guarded = mf < 1e-3 * M.h2_info()["norm_inf"]
     assert np.array_equal(cm[guarded], cf[guarded])
+
+
+def test_mixed_wide_blocks_counts_away_from_spectrum(pkg):
+    """Blocks of up to 128 rows (leaf 128): the FP32 Schur tiles are 64 wide,
+    so diagonal blocks span 2 x 2 tiles and their upper tile is written as the
+    transpose of the lower one.  Counts more than Delta from the spectrum equal
+    the dense oracle's."""
+    X = W.uniform_cube(2048, 2, 31)
+    kp = (1e-3, 0, 0, 0)
+    A = dense.kernel_matrix(W.LAPLACE_EPS, kp, X)
+    ev = dense.eigenvalues(A)
+    M = pkg.H2Matrix(X, W.LAPLACE_EPS, kp, leaf=128, rank=32, max_lanes=64, precision=pkg.H2_PREC_MIXED)
+    delta = 64 * 2.0 ** -24 * M.h2_info()["norm_inf"]
+    gaps = np.nonzero(np.diff(ev) > 4 * delta)[0]
+    shifts = 0.5 * (ev[gaps] + ev[gaps + 1])[::7][:64]
+    assert len(shifts) >= 32
+    cm, _ = M.h2_inertia(shifts)
+    assert np.array_equal(cm, [np.sum(ev < s) for s in shifts])
+    assert M.h2_status()[0] == 0
+    M.close()
