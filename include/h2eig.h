@@ -100,12 +100,13 @@ typedef struct {
                             redundant rows of all fill blocks of a row, Sec.
                             3.4) may reach this many columns runs on a cluster
                             of 8 CTAs; 0 = 4096, < 0 = never */
-    int autotune;        /* 1: at build, time both Bunch-Kaufman kernels (one
-                            warp or one 256-thread CTA per block) and both
-                            recompression kernels (one CTA, 8-CTA cluster) on
-                            full batches of shifts over the Gershgorin interval
-                            and keep the faster per level (overrides
-                            recomp_cluster_cols); 0 (default): fixed rules */
+    int autotune;        /* 1: at build, time the Bunch-Kaufman kernels (one
+                            warp, one 128-thread or one 256-thread CTA per
+                            block) and both recompression kernels (one CTA,
+                            8-CTA cluster) on full batches of shifts over the
+                            Gershgorin interval and keep the fastest per level
+                            (overrides recomp_cluster_cols); 0 (default):
+                            fixed rules */
 } h2_options;
 
 /* Fills *opt with the defaults above.  Never fails. */
@@ -164,7 +165,7 @@ int h2_inertia_device(h2_handle h, const double* d_shifts, int64_t ns, int64_t* 
 /*
  * h2_autotune_choice -- the kernel choices of one level (0 = root .. L =
  * leaves): out[0] = threads per Bunch-Kaufman block factorization (32: one
- * warp per block, for blocks up to 64; 256: one CTA), out[1] = 1 if the fill
+ * warp per block, for blocks up to 64; 128 or 256: one CTA), out[1] = 1 if the fill
  * recompression runs on an 8-CTA cluster, else 0.  Reports the fixed rules
  * when the handle was built without autotune.
  *   out: host, 2 ints.  Errors: H2_ERR_INVALID_ARG.

@@ -2415,10 +2415,12 @@ static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, 
     return nl;
 }
 
-// Autotuning (h2_options.autotune): both candidates of every per-level
-// choice run on full batches of shifts spread over the Gershgorin interval;
-// each launch is timed with CUDA events on the handle's stream (the second of
-// two runs per candidate, warm), and every level keeps its faster kernel.
+// Autotuning (h2_options.autotune): every candidate of each per-level choice
+// (Bunch-Kaufman: one warp, 128 or 256 threads per block; recompression: one
+// CTA or a cluster) runs on full batches of shifts spread over the Gershgorin
+// interval; each launch is timed with CUDA events on the handle's stream (the
+// second of two runs per pass, warm), and every level keeps its fastest
+// kernel.
 static int autotune(h2_matrix* h) {
     const int L = h->plan.L;
     Workspace& ws = h->ws;
@@ -2430,9 +2432,12 @@ static int autotune(h2_matrix* h) {
     for (int i = 0; i < LN; ++i) sh[i] = h->glo + (h->ghi - h->glo) * (i + 0.5) / LN;
     CK(cudaMemcpyAsync(ws.d_shifts, sh.data(), LN * sizeof(double), cudaMemcpyHostToDevice, st));
     k_set_int<<<1, 1, 0, st>>>(fs->d_active, LN);
-    const int cand_ldl[2] = {32, NT}, cand_rc[2] = {0, 1};   // 32: one warp per block (blocks <= 64)
-    std::vector<double> t_ldl[2], t_rc[2];
-    for (int c = 0; c < 2; ++c) {
+    // pass c runs LDL candidate c and recompression candidate c % 2
+    constexpr int NPASS = 3;
+    const int cand_ldl[NPASS] = {32, NT, 128};   // 32: one warp per block (blocks <= 64)
+    const int cand_rc[NPASS] = {0, 1, 0};
+    std::vector<double> t_ldl[NPASS], t_rc[NPASS];
+    for (int c = 0; c < NPASS; ++c) {
         t_ldl[c].assign(L + 1, 0.0);
         t_rc[c].assign(L + 1, 0.0);
         h->tune_ldl.assign(L + 1, cand_ldl[c]);
@@ -2461,8 +2466,12 @@ static int autotune(h2_matrix* h) {
         }
     }
     for (int l = 0; l <= L; ++l) {
-        h->tune_ldl[l] = t_ldl[0][l] <= t_ldl[1][l] ? cand_ldl[0] : cand_ldl[1];
-        h->tune_recomp[l] = t_rc[0][l] <= t_rc[1][l] ? cand_rc[0] : cand_rc[1];
+        int bl = 0;
+        for (int c = 1; c < NPASS; ++c)
+            if (t_ldl[c][l] < t_ldl[bl][l]) bl = c;
+        h->tune_ldl[l] = cand_ldl[bl];
+        const double t0 = std::min(t_rc[0][l], t_rc[2][l]);
+        h->tune_recomp[l] = t0 <= t_rc[1][l] ? cand_rc[0] : cand_rc[1];
     }
     CK(cudaMemsetAsync(ws.d_err, 0, 8 * sizeof(int), st));
     CK(cudaStreamSynchronize(st));

@@ -105,7 +105,7 @@ def test_autotuned_handle(pkg):
         L = M.h2_info()["levels"] - 1
         for l in range(L + 1):
             t, c = M.h2_autotune_choice(l)
-            assert t in (32, 256) and c in (0, 1)
+            assert t in (32, 128, 256) and c in (0, 1)
         got, mp = M.h2_inertia(s)
         assert np.array_equal(got[sure], want[sure])
         assert M.h2_status()[0] == 0
