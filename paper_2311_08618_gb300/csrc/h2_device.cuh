@@ -432,12 +432,7 @@ __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, doubl
     __syncthreads();
 }
 
-// The same Bunch-Kaufman LDL^T as cta_bk_ldl, run by one warp: the same
-// pivot search (largest |value|, first index on ties), the same decisions and
-// the same expression for every updated element, with warp shuffles for the
-// reductions and __syncwarp for the barriers.  The trailing update walks the
-// (row, column) pairs of the trailing block as one flat index, so no lane
-// idles on a partial row.  neg / minpiv / bad are lane 0's accumulators.
+// argmax over a warp: the largest v, the smallest index on ties
 __device__ __forceinline__ void warp_argmax(double& v, int& idx) {
     for (int o = 16; o > 0; o >>= 1) {
         double ov = __shfl_xor_sync(0xffffffffu, v, o);
@@ -446,6 +441,57 @@ __device__ __forceinline__ void warp_argmax(double& v, int& idx) {
     }
 }
 
+// Trailing update of one Bunch-Kaufman step on a warp:
+//   S[o + i][o + j] -= a[o + i] * b[o + j]                        (1x1 pivot)
+//   S[o + i][o + j] -= a[o + i] * b[o + j] + a2[o + i] * b2[o + j]  (2x2 pivot)
+// for i, j < t.  The lanes walk the flattened t x t block 32 elements apart
+// (di rows and dj columns per step); each lane loads four elements before it
+// stores any, so their products overlap in the FP64 pipe.
+template <bool TWO>
+__device__ __forceinline__ void warp_trailing_update(double* S, int lds, int o, int t, const double* a,
+                                                     const double* b, const double* a2, const double* b2) {
+    const int lane = threadIdx.x & 31;
+    const int di = 32 / t, dj = 32 % t;
+    int i = lane / t, j = lane % t;
+    int e = lane;
+    for (; e + 96 < t * t; e += 128) {
+        int ii[4], jj[4];
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            ii[u] = o + i;
+            jj[u] = o + j;
+            i += di;
+            j += dj;
+            if (j >= t) { j -= t; ++i; }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = S[(size_t)ii[u] * lds + jj[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (TWO) v[u] -= a[ii[u]] * b[jj[u]] + a2[ii[u]] * b2[jj[u]];
+            else v[u] -= a[ii[u]] * b[jj[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) S[(size_t)ii[u] * lds + jj[u]] = v[u];
+    }
+    for (; e < t * t; e += 32) {
+        const int ig = o + i, jg = o + j;
+        if (TWO) S[(size_t)ig * lds + jg] -= a[ig] * b[jg] + a2[ig] * b2[jg];
+        else S[(size_t)ig * lds + jg] -= a[ig] * b[jg];
+        i += di;
+        j += dj;
+        if (j >= t) { j -= t; ++i; }
+    }
+}
+
+// The same Bunch-Kaufman LDL^T as cta_bk_ldl, run by one warp: the same
+// pivot search (largest |value|, first index on ties), the same decisions and
+// the same expression for every updated element, with warp shuffles for the
+// reductions and __syncwarp for the barriers.  The trailing update walks the
+// (row, column) pairs of the trailing block as one flat index, so no lane
+// idles on a partial row (warp_trailing_update).  neg / minpiv / bad are
+// lane 0's accumulators.
 __device__ inline void warp_bk_ldl(double* S, int lds, int n, int* perm, int* piv, int* neg, double* minpiv, int* bad,
                             double zero_pivot, double* buf) {
     const double alpha = (1.0 + sqrt(17.0)) / 8.0;
@@ -532,16 +578,7 @@ __device__ inline void warp_bk_ldl(double* S, int lds, int n, int* perm, int* pi
                     l0[i] = c * invd;
                 }
                 __syncwarp();
-                {   // flat (row, column) walk, stepping 32 = di rows + dj columns
-                    const int di = 32 / t, dj = 32 % t;
-                    int i = lane / t, j = lane % t;
-                    for (int e = lane; e < t * t; e += 32) {
-                        S[(size_t)(k + 1 + i) * lds + k + 1 + j] -= l0[k + 1 + i] * c0[k + 1 + j];
-                        i += di;
-                        j += dj;
-                        if (j >= t) { j -= t; ++i; }
-                    }
-                }
+                warp_trailing_update<false>(S, lds, k + 1, t, l0, c0, nullptr, nullptr);
                 for (int i = k + 1 + lane; i < n; i += 32) S[(size_t)i * lds + k] = l0[i];
             }
             __syncwarp();
@@ -572,17 +609,7 @@ __device__ inline void warp_bk_ldl(double* S, int lds, int n, int* perm, int* pi
                     l1[i] = ci0 * i01 + ci1 * i11;
                 }
                 __syncwarp();
-                {
-                    const int di = 32 / t, dj = 32 % t;
-                    int i = lane / t, j = lane % t;
-                    for (int e = lane; e < t * t; e += 32) {
-                        const int ii = k + 2 + i, jj = k + 2 + j;
-                        S[(size_t)ii * lds + jj] -= l0[ii] * c0[jj] + l1[ii] * c1[jj];
-                        i += di;
-                        j += dj;
-                        if (j >= t) { j -= t; ++i; }
-                    }
-                }
+                warp_trailing_update<true>(S, lds, k + 2, t, l0, c0, l1, c1);
                 for (int i = k + 2 + lane; i < n; i += 32) {
                     S[(size_t)i * lds + k] = l0[i];
                     S[(size_t)i * lds + k + 1] = l1[i];
