@@ -593,16 +593,17 @@ def _circle_sweep(args):
 
 
 def _tune_summary(mats):
-    """(levels with one warp per Bunch-Kaufman block, levels with a clustered
-    recompression) / levels, over all handles."""
-    n = t128 = clu = 0
+    """Levels per Bunch-Kaufman kernel (one warp, 128- or 256-thread CTA per
+    block) and levels with a clustered recompression, over all handles."""
+    n = clu = 0
+    per = {32: 0, 128: 0, 256: 0}
     for M in mats:
         for l in range(M.h2_info()["levels"]):
             t, c = M.h2_autotune_choice(l)
             n += 1
-            t128 += t == 32
+            per[int(t)] = per.get(int(t), 0) + 1
             clu += c
-    return "%d/%d, %d/%d" % (t128, n, clu, n)
+    return "%d/%d/%d of %d, %d/%d" % (per[32], per[128], per[256], n, clu, n)
 
 
 def _batching(args):
@@ -646,7 +647,7 @@ def _batching(args):
            "max_abs_diff_vs_sequential": float(np.max(np.abs(lam_g - lam_s))), "tol": tol,
            "build_s": build_s, "autotune": "per level: Bunch-Kaufman on one warp or one CTA per block, "
                                             "recompression on one CTA or an 8-CTA cluster, timed at build; "
-                                            "levels choosing (warp, clustered): %s" % _tune_summary(mats)}
+                                            "levels choosing (warp/128/256 threads, clustered): %s" % _tune_summary(mats)}
     G.close()
     for M in mats:
         M.close()
