@@ -227,3 +227,75 @@ def test_weak_unit_circle_counts():
     for mu, g in zip(shifts, gap):
         if g > 1e-3:
             assert h2.h2_inertia(h, mu)[0] == int(np.sum(ev < mu))
+
+
+
+def _near_eigenvalue_shifts(At):
+    """Shifts at lambda_j(A~) -+ 1e-7 ||A~||_inf for every 16th j: the
+    factorization error of the generalized LDL (truncation 1e-10 ||A||) is far
+    below that distance, while a wrong recompression is not."""
+    evt = np.linalg.eigvalsh(At)
+    d = 1e-7 * np.abs(At).sum(axis=1).max()
+    return evt, np.concatenate([evt[::16] - d, evt[::16] + d])
+
+
+def test_counts_next_to_eigenvalues(lap2d):
+    """nu(A~ - mu I) equals the dense count of A~ for shifts within
+    1e-7 ||A~|| of its eigenvalues (the fill-ins of this matrix are
+    recompressed at several levels)."""
+    h, A, At = lap2d
+    evt, sel = _near_eigenvalue_shifts(At)
+    for mu in sel:
+        assert h2.h2_inertia(h, mu)[0] == int(np.sum(evt < mu))
+
+
+def _lap2d_wrong_counts(h, At):
+    evt, sel = _near_eigenvalue_shifts(At)
+    return sum(h2.h2_inertia(h, mu)[0] != int(np.sum(evt < mu)) for mu in sel)
+
+
+def _min_matrix_wrong_counts(h, n):
+    ev = min_eigs(n)
+    return sum(h2.h2_inertia(h, mu)[0] != int(np.sum(ev < mu)) for mu in gaps_shifts(ev, 2))
+
+
+@pytest.mark.parametrize("mistake", ["schur_sign", "no_recompression", "transposed_solve", "rotation_side"])
+def test_planted_mistakes_are_caught(monkeypatch, lap2d, mistake):
+    """A plausible mistake planted in the H^2 oracle (a wrong sign in the
+    Schur update, the recompression left out, the triangular solve with the
+    transposed factor, the rotation by V^T instead of V) must break a pin: the
+    closed form of the min(i, j) matrix, or the dense counts of the 2D Laplace
+    A~ next to its eigenvalues (recompression of the min matrix's fill-ins
+    adds no columns, so only the second pin sees the last two)."""
+    n = 90
+    h = h2.construct(W.line_points(n), W.MIN_TEST, (0, 0, 0, 0), 12, 8, 1.0)
+    hl, _, At = lap2d
+    assert _min_matrix_wrong_counts(h, n) == 0 and _lap2d_wrong_counts(hl, At) == 0
+    if mistake == "schur_sign":
+        def add(self, a, b, ra, rb, delta):
+            if a >= b:
+                self.blk[(a, b)][np.ix_(ra, rb)] += delta
+            else:
+                self.blk[(b, a)][np.ix_(rb, ra)] += delta.T
+        monkeypatch.setattr(h2._Level, "sub", add)
+    elif mistake == "no_recompression":
+        monkeypatch.setattr(h2, "_recompress", lambda *a, **k: None)
+    elif mistake == "transposed_solve":
+        orig = h2.solve_triangular
+        monkeypatch.setattr(h2, "solve_triangular",
+                            lambda L, B, lower=True, unit_diagonal=False: orig(L.T, B, lower=not lower,
+                                                                               unit_diagonal=unit_diagonal))
+    else:
+        orig_qr = h2.pivoted_qr_basis
+
+        def qr_transposed(Y, tol, cap):
+            V, t = orig_qr(Y, tol, cap)
+            return V.T.copy(), t
+        monkeypatch.setattr(h2, "pivoted_qr_basis", qr_transposed)
+
+    def caught(check):      # wrong counts, or the oracle breaking down, fail the pin
+        try:
+            return check() > 0
+        except np.linalg.LinAlgError:
+            return True
+    assert caught(lambda: _min_matrix_wrong_counts(h, n)) or caught(lambda: _lap2d_wrong_counts(hl, At))
