@@ -93,6 +93,29 @@ def test_laplace2d_counts_match_oracle(pkg):
     _compare_with_oracle(pkg, X, W.LAPLACE_EPS, kp, 32, 16, s)
 
 
+def test_laplace2d_counts_next_to_eigenvalues(pkg):
+    """Shifts within 1e-7 ||A~|| of the eigenvalues of the oracle's A~ (every
+    8th one, both sides): far above the factorization error of either side,
+    far below the effect of a wrong recompression (the oracle's planted
+    mistakes flip such counts), so the GPU's recompression and rotation are
+    pinned, not only its pivots."""
+    X = W.uniform_cube(256, 2, 21)
+    kp = (1e-3, 0, 0, 0)
+    ref = oh2.construct(X, W.LAPLACE_EPS, kp, 32, 16, 1.0)
+    At = oh2.dense_approximation(ref)
+    evt = np.linalg.eigvalsh(At)
+    d = 1e-7 * np.abs(At).sum(axis=1).max()
+    s = np.concatenate([evt[::8] - d, evt[::8] + d])
+    M = pkg.H2Matrix(X, W.LAPLACE_EPS, kp, leaf=32, rank=16, max_lanes=64)
+    got, mp = M.h2_inertia(s)
+    want = np.array([np.sum(evt < x) for x in s])
+    sure = mp > 1e-10 * ref.scale
+    assert sure.sum() >= 0.9 * len(s)
+    assert np.array_equal(got[sure], want[sure])
+    assert M.h2_status()[0] == 0
+    M.close()
+
+
 def test_yukawa3d_ragged_counts_match_oracle(pkg):
     X = W.uniform_cube(300, 3, 22)          # leaves of 37 and 38 points
     kp = (1e-3, 0, 0, 0)
