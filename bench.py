@@ -536,13 +536,15 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
             "batching": batching_res}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        sample = list(sh[args.warmup][:: max(1, lanes // (2 * cores))][:2 * cores])
+        # up to 16 shifts per core (all 256 shifts of the step on 16 cores): about
+        # 10-30 s of CPU work, a couple of seconds of wall time
+        sample = list(sh[args.warmup][:: max(1, lanes // (16 * cores))][:16 * cores])
         rate, secs, ocounts = oracle_throughput(sample, cores)
         got = {s: int(c) for s, c in zip(sh[args.warmup], cnt_fp64[args.warmup].cpu().numpy())}
         agree = sum(int(got[s] == ocounts[s]) for s in sample)
         line["cpu_baseline"] = {"value": rate, "unit": "shifts/s", "cores": cores, "kind": "oracle",
-                                "sample": "%d shifts of step 1 (%.1f s wall, one process per core)" %
-                                          (len(sample), secs),
+                                "sample": "%d shifts of step 1 (%.1f s wall, about %.0f s of CPU work, "
+                                          "one process per core)" % (len(sample), secs, secs * cores),
                                 "counts_equal_to_gpu": "%d/%d" % (agree, len(sample))}
     if rank == 0:
         print(json.dumps(line), flush=True)
