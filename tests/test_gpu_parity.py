@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
-Bar (the benchmark spec): counts bit-exact with the H^2 oracle for every shift whose
+Bar: counts bit-exact with the H^2 oracle for every shift whose
 smallest |pivot| exceeds 1e-10 * ||A||; closed-form matrices exactly; k-th
 eigenvalues within tol + 1e-8 ||A|| of the dense oracle.
 """
