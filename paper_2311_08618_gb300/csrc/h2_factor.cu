@@ -1199,6 +1199,22 @@ constexpr int JB = 8;
 // T is the arithmetic of the solve and the type W and Y are stored in: double
 // (FP64 path) or float (mixed path: the FP64 factor L, D of the LDL step is
 // rounded to FP32, as are the products that form the Schur update)
+// 1 / d_j for a 1x1 pivot at j, 1 / det for a 2x2 pivot starting at j (0
+// elsewhere), from the factor's entries rounded to T: Y = W D^-1 then
+// multiplies by it instead of dividing once per element
+template <typename T>
+__device__ __forceinline__ T pivot_reciprocal(const double* F, int D, int Rp, const int* piv, int j) {
+    const int pv = piv[j];
+    const bool two = pv == 2 && j + 1 < Rp;
+    if (pv != 1 && !two) return (T)0;
+    T x = (T)F[(size_t)j * D + j];
+    if (two) {
+        const T b0 = (T)F[(size_t)(j + 1) * D + j], c0 = (T)F[(size_t)(j + 1) * D + j + 1];
+        x = x * c0 - b0 * b0;
+    }
+    return (T)1 / x;
+}
+
 template <typename T>
 __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_smem, const int bx, const int by) {
     HbScope hb_(4);
@@ -1254,7 +1270,8 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
         T* sWm = sLz + (size_t)Rp * ldl;                         // rows x (Rp + 1)
         T* sDg = sWm + (size_t)rows * (Rp + 1);
         T* sOd = sDg + Rp;
-        int* sPerm = reinterpret_cast<int*>(sOd + Rp);
+        T* sRc = sOd + Rp;      // 1 / d of a 1x1 pivot, 1 / det at the first column of a 2x2
+        int* sPerm = reinterpret_cast<int*>(sRc + Rp);
         int* sPiv = sPerm + Rp;
         const int ldw = Rp + 1;
         for (int e = threadIdx.x; e < Rp * Rp; e += NT) {
@@ -1262,8 +1279,10 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
             sLz[j * ldl + k] = (k < j && !(piv[k] == 2 && j == k + 1)) ? (T)F[(size_t)j * D + k] : (T)0;
         }
         for (int j = threadIdx.x; j < Rp; j += NT) {
-            sDg[j] = (T)F[(size_t)j * D + j];
+            const T dj = (T)F[(size_t)j * D + j];
+            sDg[j] = dj;
             sOd[j] = (piv[j] == 2 && j + 1 < Rp) ? (T)F[(size_t)(j + 1) * D + j] : (T)0;
+            sRc[j] = pivot_reciprocal<T>(F, D, Rp, piv, j);
             sPerm[j] = perm[j];
             sPiv[j] = piv[j];
         }
@@ -1303,11 +1322,11 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
             const T* wi = sWm + i * ldw;
             T v;
             if (sPiv[j] == 1) {
-                v = wi[j] * ((T)1 / sDg[j]);
+                v = wi[j] * sRc[j];
             } else {
                 const int j0 = sPiv[j] == 2 ? j : j - 1;
-                const T a0 = sDg[j0], b0 = sOd[j0], c0 = sDg[j0 + 1];
-                const T idet = (T)1 / (a0 * c0 - b0 * b0);
+                const T b0 = sOd[j0], c0 = sDg[j0 + 1], a0 = sDg[j0];
+                const T idet = sRc[j0];
                 const T w0 = wi[j0], w1 = wi[j0 + 1];
                 v = (j == j0) ? (w0 * c0 - w1 * b0) * idet : (w1 * a0 - w0 * b0) * idet;
             }
@@ -1323,8 +1342,10 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
         const int* sperm = perm;
         const int* spiv = piv;
         const int ldl = Rp + 1;                                      // padded as in the path above
+        T* sRc = reinterpret_cast<T*>(sh);                           // Rp pivot reciprocals
+        for (int j = threadIdx.x; j < Rp; j += NT) sRc[j] = pivot_reciprocal<T>(F, D, Rp, piv, j);
         if (use_smem) {
-            T* L2 = reinterpret_cast<T*>(sh);                        // Rp x (Rp + 1)
+            T* L2 = sRc + Rp;                                        // Rp x (Rp + 1)
             int* p2 = reinterpret_cast<int*>(L2 + (size_t)Rp * ldl);
             int* v2 = p2 + Rp;
             for (int e = threadIdx.x; e < Rp * Rp; e += NT) L2[(e / Rp) * ldl + e % Rp] = (T)F[(size_t)(e / Rp) * D + e % Rp];
@@ -1372,11 +1393,11 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
             const T* wi = W + (size_t)i * D;
             T v;
             if (spiv[j] == 1) {
-                v = wi[j] * ((T)1 / Fx(j, j));
+                v = wi[j] * sRc[j];
             } else {
                 int j0 = spiv[j] == 2 ? j : j - 1;
                 T a0 = Fx(j0, j0), b0 = Fx(j0 + 1, j0), c0 = Fx(j0 + 1, j0 + 1);
-                T idet = (T)1 / (a0 * c0 - b0 * b0);
+                T idet = sRc[j0];
                 T w0 = wi[j0], w1 = wi[j0 + 1];
                 v = (j == j0) ? (w0 * c0 - w1 * b0) * idet : (w1 * a0 - w0 * b0) * idet;
             }
@@ -2299,16 +2320,18 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
                 R.push_back(q);
             }
             {
-                const size_t sm_trsm = (size_t)Dm * (Dm + 1) * sizeof(double) + 2 * (size_t)Dm * sizeof(int);
-                // flag 2: L, D and W staged (Rp (Rp + 1) + rows (Rp + 1) + 2 Rp values, 2 Rp ints)
-                const size_t sm_full = ((size_t)Dm * (Dm + 1) + (size_t)Dm * (Dm + 1) + 2 * (size_t)Dm) * sizeof(double) +
+                // flags 0 and 1: Rp pivot reciprocals, then (flag 1) L and the pivots
+                const size_t sm_rc = (size_t)Dm * sizeof(double);
+                const size_t sm_trsm = sm_rc + (size_t)Dm * (Dm + 1) * sizeof(double) + 2 * (size_t)Dm * sizeof(int);
+                // flag 2: L, D and W staged (Rp (Rp + 1) + rows (Rp + 1) + 3 Rp values, 2 Rp ints)
+                const size_t sm_full = ((size_t)Dm * (Dm + 1) + (size_t)Dm * (Dm + 1) + 3 * (size_t)Dm) * sizeof(double) +
                                        2 * (size_t)Dm * sizeof(int);
                 LaunchRec q = r;
                 q.op = OP_TRSM;
                 q.kind = H2_KIND_TRSM;
                 q.flag = sm_full <= kSmemCap ? 2 : (sm_trsm <= kSmemCap ? 1 : 0);
                 q.variant = mixed ? 1 : 0;
-                q.smem = q.flag == 2 ? sm_full : (q.flag ? sm_trsm : 0);
+                q.smem = q.flag == 2 ? sm_full : (q.flag ? sm_trsm : sm_rc);
                 q.grid = dim3(C.ncl * C.ntarg_max, LN);
                 R.push_back(q);
             }
