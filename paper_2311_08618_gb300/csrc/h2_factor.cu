@@ -174,8 +174,9 @@ __device__ __forceinline__ double& belem(double* B, int D, int trans, int i, int
 // Symmetric Schur updates.  The update of a diagonal block, S_aa -= W_a Y_a^T
 // = W_a D^-1 W_a^T, is symmetric: only the tiles on and below the tile
 // diagonal are computed, and each lower tile also writes its transpose into
-// the skipped upper tile.  Live entries of an r x r block covered by those
-// tiles (ts x ts):
+// the skipped upper tile (the DFMA kernel computes only the lower triangle of
+// a diagonal tile as well).  Live entries of an r x r block covered by the
+// tiles on and below the tile diagonal (ts x ts):
 __device__ __forceinline__ double lower_tile_entries(int r, int ts) {
     double s = 0.0;
     for (int i0 = 0; i0 < r; i0 += ts) s += (double)min(ts, r - i0) * min(r, i0 + ts);
@@ -1242,7 +1243,11 @@ __device__ __forceinline__ void k_trsm_body(const FactorArgs& A, const int use_s
         for (int tj = 0; tj <= ti; ++tj) {
             int b2 = A.targ[ci * A.ntarg_max + tj];
             double rb = (b2 == p) ? rk1 : live_rows(A, b2, lane);
-            const double ent = tj == ti ? lower_tile_entries(rows, sizeof(T) == 4 ? TSF : TS) : rows * rb;
+            // a diagonal block: its lower triangle (DFMA kernel) or the tiles
+            // on and below the tile diagonal (FP32 and digit kernels)
+            const double ent = tj != ti ? rows * rb
+                             : (sizeof(T) == 8 && A.lay.dk == 0) ? 0.5 * rows * (rows + 1.0)
+                                                                 : lower_tile_entries(rows, sizeof(T) == 4 ? TSF : TS);
             fs += 2.0 * ent * Rp;
             bs += 8.0 * (rows * (double)Rp + rb * Rp + 2.0 * rows * rb);
         }
@@ -1478,6 +1483,56 @@ __device__ __forceinline__ void schur_rows(const T (*sR)[TS + 1], const T (*sC)[
     }
 }
 
+// Diagonal tile (i0, i0) of a symmetric update S_aa -= W_a Y_a^T: only its
+// nr (nr + 1) / 2 entries on and below the diagonal are computed (up to three
+// per thread, the rows of W and of Y staged in sR / sC as for a full tile,
+// each entry summed over k in the same order), and each is written to (r, c)
+// and (c, r).  Entry t of the lower triangle is (r, c), t = r (r + 1) / 2 + c.
+__device__ __forceinline__ void tri_index(int t, int& r, int& c) {
+    r = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    while (r > 0 && r * (r + 1) / 2 > t) --r;
+    c = t - r * (r + 1) / 2;
+}
+template <typename T>
+__device__ __forceinline__ void schur_diag_tile(double* B, int D, int trans, const T* W, const T* Y, int i0, int nr,
+                                                int Rp, T (*sR)[TS + 1], T (*sC)[TS + 1]) {
+    const int ne = nr * (nr + 1) / 2;
+    T acc[3] = {0, 0, 0};
+    for (int k0 = 0; k0 < Rp; k0 += TS) {
+        const int kc = min(TS, Rp - k0);
+        for (int e = threadIdx.x; e < TS * TS; e += NT) {
+            const int r = e / TS, k = e % TS;
+            sR[r][k] = (r < nr && k < kc) ? W[(size_t)(i0 + r) * D + k0 + k] : (T)0;
+            sC[r][k] = (r < nr && k < kc) ? Y[(size_t)(i0 + r) * D + k0 + k] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const int t = threadIdx.x + NT * u;
+            if (t < ne) {
+                int r, c;
+                tri_index(t, r, c);
+                T a = acc[u];
+#pragma unroll 8
+                for (int k = 0; k < kc; ++k) a += sR[r][k] * sC[c][k];
+                acc[u] = a;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+        const int t = threadIdx.x + NT * u;
+        if (t < ne) {
+            int r, c;
+            tri_index(t, r, c);
+            belem(B, D, trans, i0 + r, i0 + c) -= (double)acc[u];
+            if (c != r) belem(B, D, trans, i0 + c, i0 + r) -= (double)acc[u];
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void k_schur_body(const SchurArgs& A, const int bx, const int by) {
     HbScope hb_(5);
@@ -1498,6 +1553,14 @@ __device__ __forceinline__ void k_schur_body(const SchurArgs& A, const int bx, c
     const int i0 = (tile / A.tdim) * TS, j0 = (tile % A.tdim) * TS;
     if (i0 >= ra || j0 >= rb) return;
     if (P.ta == P.tb && j0 > i0) return;           // written by the mirror of tile (j0, i0)
+    __shared__ T sR[TS][TS + 1], sC[TS][TS + 1];
+    if (P.ta == P.tb && j0 == i0) {                // its lower triangle only
+        schur_diag_tile<T>(slot_ptr(A.slots, P.slot, A.lanes, lane, D), D, P.trans,
+                           reinterpret_cast<const T*>(scr + A.lay.w + (size_t)P.ta * D * D),
+                           reinterpret_cast<const T*>(scr + A.lay.y + (size_t)P.tb * D * D), i0,
+                           min(TS, ra - i0), Rp, sR, sC);
+        return;
+    }
     // kept in shared memory, not in a register through the k loop (the
     // loop's first barrier publishes it)
     __shared__ int s_mirror;
@@ -1513,7 +1576,6 @@ __device__ __forceinline__ void k_schur_body(const SchurArgs& A, const int bx, c
     const T* Rm = tp ? Y + (size_t)j0 * D : W + (size_t)i0 * D;    // row operand
     const T* Cm = tp ? W + (size_t)i0 * D : Y + (size_t)j0 * D;    // column operand
     const int nrow = tp ? nc : nr, ncol = tp ? nr : nc;
-    __shared__ T sR[TS][TS + 1], sC[TS][TS + 1];
     const int tx = threadIdx.x % TS, ty = threadIdx.x / TS;   // ty in 0..7
     const int nu = max(0, min(4, (nrow - ty + 7) / 8));
     T acc[4] = {0, 0, 0, 0};
