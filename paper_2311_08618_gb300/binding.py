@@ -205,7 +205,8 @@ class H2Matrix:
         return p
 
     def h2_autotune_choice(self, level):
-        """(threads per Bunch-Kaufman block: 32 for one warp, 128 or 256 for a CTA; 1 if the recompression is clustered) of a level."""
+        """(threads per Bunch-Kaufman block: 32 for one warp, 128 or 256 for a
+        CTA; 1 if the recompression is clustered) of a level."""
         out = np.zeros(2, dtype=np.int32)
         _check(lib().h2_autotune_choice(self._h, int(level), out.ctypes.data_as(C.c_void_p)))
         return int(out[0]), int(out[1])
