@@ -72,6 +72,52 @@ class _Resident:
     h_counts: object = None
 
 
+def plan_shifts(intervals, lanes):
+    """The shifts of one round on one matrix: the first `lanes` distinct
+    intervals (in order) share its lanes, each cut at q equally spaced
+    interior points ((q+1)-section, Algorithm 1 with spare lanes)."""
+    ivs = []
+    seen = set()
+    for key in intervals:
+        if key not in seen:
+            seen.add(key)
+            ivs.append(key)
+    if not ivs:
+        return []
+    m = min(len(ivs), lanes)
+    q, extra = divmod(lanes, m)
+    shifts = []
+    for u in range(m):
+        a, b = ivs[u]
+        qu = q + (1 if u < extra else 0)
+        shifts += [a + (b - a) * j / (qu + 1) for j in range(1, qu + 1)]
+    return shifts
+
+
+def narrow(lo, hi, k, shifts, counts):
+    """[lo, hi] narrowed by every evaluated (mu, nu) inside it: nu >= k moves
+    hi down to mu, nu < k moves lo up to mu (Algorithm 1)."""
+    for mu, nu in zip(shifts, counts):
+        if lo < mu < hi:
+            if nu >= k:
+                hi = mu
+            else:
+                lo = mu
+    return lo, hi
+
+
+def tightest_bracket(lo0, hi0, table_mu, table_nu, k):
+    """The tightest [mu_lo, mu_hi] with nu(mu_lo) < k <= nu(mu_hi) in a table
+    of evaluated (mu, nu) pairs, starting from [lo0, hi0] (Sec. 4.2)."""
+    lo, hi = lo0, hi0
+    for mu, nu in zip(table_mu, table_nu):
+        if nu < k:
+            lo = max(lo, mu)
+        else:
+            hi = min(hi, mu)
+    return lo, hi
+
+
 class Server:
     """Resident matrices + request queue + continuous batching (see module doc)."""
 
@@ -170,13 +216,7 @@ class Server:
 
     def _bracket(self, r: _Resident, k: int):
         """Tightest [mu_lo, mu_hi] from the (mu, nu) table: nu(mu_lo) < k <= nu(mu_hi)."""
-        lo, hi = r.lo0, r.hi0
-        for mu, nu in zip(r.table_mu, r.table_nu):
-            if nu < k:
-                lo = max(lo, mu)
-            else:
-                hi = min(hi, mu)
-        return lo, hi
+        return tightest_bracket(r.lo0, r.hi0, r.table_mu, r.table_nu, k)
 
     def _admit(self):
         keep = []
@@ -206,21 +246,7 @@ class Server:
             if not r.active:
                 continue
             # distinct active intervals share the lanes
-            ivs = []
-            seen = set()
-            for req in r.active:
-                key = (req.lo, req.hi)
-                if key not in seen:
-                    seen.add(key)
-                    ivs.append(key)
-            m = min(len(ivs), r.lanes)
-            q, extra = divmod(r.lanes, m)
-            shifts = []
-            for u in range(m):
-                a, b = ivs[u]
-                qu = q + (1 if u < extra else 0)
-                shifts += [a + (b - a) * j / (qu + 1) for j in range(1, qu + 1)]
-            plans[r.name] = shifts
+            plans[r.name] = plan_shifts([(req.lo, req.hi) for req in r.active], r.lanes)
         if not plans:
             self.ticks += 1
             return 0
@@ -268,12 +294,7 @@ class Server:
                 r.table_nu.insert(i, int(nu))
             still = []
             for req in r.active:
-                for mu, nu in zip(shifts, counts):
-                    if req.lo < mu < req.hi:
-                        if nu >= req.k:
-                            req.hi = mu
-                        else:
-                            req.lo = mu
+                req.lo, req.hi = narrow(req.lo, req.hi, req.k, shifts, counts)
                 req.rounds += 1
                 if req.hi - req.lo < req.tol:
                     self._finish(req)
