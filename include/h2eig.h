@@ -72,7 +72,8 @@ typedef struct {
                             updates in FP64; guarded shifts re-run in FP64
                             (see h2_inertia, h2_kth_eig) */
 #define H2_PREC_FP64_TC 2 /* as H2_PREC_FP64, but the Schur-update products
-                            W_a Y_b^T run on the tensor cores: 8 exact 7-bit
+                            W_a Y_b^T and the rotation products (block x V)
+                            run on the tensor cores: 8 exact 7-bit
                             integer digits per FP64 entry (row-scaled), BF16
                             digit products summed exactly, one FP64 rounding
                             per entry; the error stays below 2^-53 of the
