@@ -299,3 +299,16 @@ def test_planted_mistakes_are_caught(monkeypatch, lap2d, mistake):
         except np.linalg.LinAlgError:
             return True
     assert caught(lambda: _min_matrix_wrong_counts(h, n)) or caught(lambda: _lap2d_wrong_counts(hl, At))
+
+
+def test_center_admissibility_counts_equal_dense_counts_of_a_tilde():
+    """Under the centre-distance rule (ADM_CENTER) the generalized LDL still
+    counts the eigenvalues of its own (symmetric) A~ exactly, at the midpoints
+    of A~'s spectrum."""
+    X = W.uniform_cube(256, 2, 21)
+    h = h2.construct(X, W.LAPLACE_EPS, (1e-3, 0, 0, 0), 32, 16, 1.0, rule=h2.ADM_CENTER)
+    At = h2.dense_approximation(h)
+    assert np.allclose(At, At.T, atol=1e-12 * np.abs(At).max())
+    evt = np.linalg.eigvalsh(At)
+    for mu in gaps_shifts(evt, 23):
+        assert h2.h2_inertia(h, mu)[0] == int(np.sum(evt < mu))
