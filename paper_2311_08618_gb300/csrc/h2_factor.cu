@@ -2327,8 +2327,7 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
                           C.targ_slot, C.targ_trans, C.ntarg, C.ntarg_max, C.rowblk, C.rowblk_other,
                           C.rowblk_trans, C.rowblk_fill, C.nrow, C.nrow_max, C.fillq, C.fillslot, C.nfill,
                           C.nfill_max, ws.d_scratch, W.lay, h->tol, 2.220446049250313e-16 * h->norm_inf,
-                          h->fill_cap_eff, ws.d_neg, ws.d_minpiv, ws.d_err, fs->d_active, fs->d_stats};
-            fa.ncl = C.ncl;
+                          h->fill_cap_eff, ws.d_neg, ws.d_minpiv, ws.d_err, fs->d_active, fs->d_stats, C.ncl};
             LaunchRec r;
             r.phase = 2;
             r.step = L - l;
