@@ -77,7 +77,8 @@ typedef struct {
                             integer digits per FP64 entry (row-scaled), BF16
                             digit products summed exactly, one FP64 rounding
                             per entry; the error stays below 2^-53 of the
-                            result plus 2^-56 K of the row-scale products */
+                            result plus 1.24e-16 K of the row-scale products
+                            (the powers of two above each row's entries) */
 
 typedef struct {
     int precision;       /* H2_PREC_FP64 (default), H2_PREC_MIXED or

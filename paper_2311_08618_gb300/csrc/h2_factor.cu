@@ -1629,8 +1629,10 @@ __global__ void __launch_bounds__(NT) k_schur_g(GroupArgs<SchurArgs> G) {
 // the truncated bits below 2^(e-56).  Digits are exact in BF16, so
 //   sum_k W_ik Y_jk = 2^(e_i + f_j) sum_t 2^(-7t) L_t,
 //   L_t = sum_{p+q=t} sum_k d_p(W_ik) d_q(Y_jk),
-// and the terms with t = p + q > 9 (below 2^-70 of the row scales) are dropped:
-// 36 of the 64 digit pairs remain.  Over a chunk of OZK = 32 values of k,
+// and the terms with t = p + q > 9 are dropped (each below 2^-56 of the
+// row-scale product 2^(e_i + f_j)): 36 of the 64 digit pairs remain.  With the
+// truncated bits of both operands, the error of a product of K terms stays
+// below 2^-53 of the result plus 1.24e-16 K 2^(e_i + f_j).  Over a chunk of OZK = 32 values of k,
 // |L_t| <= 8 * 32 * 127^2 < 2^22, and every partial sum an MMA forms is an
 // integer below 2^24: BF16 products with FP32 accumulation (mma.sync
 // m16n8k16) are exact.  Per chunk the level sums are folded into two exact
