@@ -26,6 +26,8 @@ CASES = [
     ("line100", lambda: W.line_points(100), 16, oh2.ADM_BOX),
     ("square512_center", lambda: W.uniform_cube(512, 2, 5), 32, oh2.ADM_CENTER),
     ("circle1024_weak", lambda: W.unit_circle(1024, 5), 64, oh2.ADM_WEAK),
+    # the 3D n = 65536 configuration (leaf 256): 191 colours at the leaf level
+    ("cube65536_leaf256", lambda: W.uniform_cube(65536, 3, 2), 256, oh2.ADM_BOX),
 ]
 
 
