@@ -69,8 +69,9 @@ typedef struct {
 #define H2_PREC_MIXED 1  /* Schur-update, triangular-solve and rotation
                             products in FP32 (FP32 accumulation); storage,
                             Bunch-Kaufman pivoting, pivot counts and interval
-                            updates in FP64; guarded shifts re-run in FP64
-                            (see h2_inertia, h2_kth_eig) */
+                            updates in FP64; counts certified, uncertified
+                            shifts re-run in FP64 (see h2_inertia,
+                            h2_kth_eig) */
 #define H2_PREC_FP64_TC 2 /* as H2_PREC_FP64, but the Schur-update products
                             W_a Y_b^T and the rotation products (block x V)
                             run on the tensor cores: 8 exact 7-bit
@@ -90,9 +91,11 @@ typedef struct {
                             recompression (Sec. 3.4); 0 = 2 * rank */
     int sketch_cols;     /* columns of the random sketch of A_{l;c,+}; 0 = rank + 16 */
     uint64_t seed;       /* SplitMix64 state for the sketch matrix */
-    int max_lanes;       /* shifts factorized concurrently; 0 = 64 */
+    int max_lanes;       /* shifts factorized concurrently, <= 65535; 0 = 64
+                            (without hbm_budget) */
     double pivot_guard;  /* mixed precision: a shift whose min |pivot| is below
-                            pivot_guard * ||A||_inf is re-run in FP64; 0 = 1e-4 */
+                            pivot_guard * ||A||_inf is re-run in FP64 (on top
+                            of the certificate of h2_inertia); 0 = 1e-4 */
     void* stream;        /* cudaStream_t for all work of the handle; NULL = a
                             stream created by the library */
     int graphs;          /* 1 (default): each batch replays a CUDA graph
@@ -109,6 +112,13 @@ typedef struct {
                             Gershgorin interval and keep the fastest per level
                             (overrides recomp_cluster_cols); 0 (default):
                             fixed rules */
+    size_t hbm_budget;   /* bytes of device memory the per-batch factorization
+                            workspace may take (admission by HBM footprint):
+                            0 (default) = no budget, max_lanes lanes; > 0 =
+                            the most lanes whose workspace fits, at most
+                            max_lanes (max_lanes = 0: no other bound); h2_build
+                            fails with H2_ERR_OOM when one lane does not fit.
+                            h2_info reports the lanes and bytes chosen */
 } h2_options;
 
 /* Fills *opt with the defaults above.  Never fails. */
@@ -148,9 +158,15 @@ const char* h2_last_error(void);
  *   counts        : host, caller-owned, ns int64.
  *   min_abs_pivot : host, caller-owned, ns FP64, or NULL.
  * Shifts are processed in batches of max_lanes.  Blocks until done.
- * H2_PREC_MIXED: each batch is factorized with FP32 Schur/rotation products;
- * a shift whose min |pivot| is below pivot_guard * ||A||_inf is factorized
- * again in FP64 and its count and pivot replaced.
+ * H2_PREC_MIXED: counts are certified (Parlett's criterion, Sec. 4.1).  The
+ * FP32 products make each mixed factorization exact for a perturbed matrix
+ * A~ + E; with Delta = 64 * 2^-24 * ||A||_inf > 2 ||E||, mixed counts at
+ * mu - Delta and mu + Delta that agree equal nu(mu).  Each shift is therefore
+ * factorized in mixed precision at mu - Delta and mu + Delta (two lanes); a
+ * shift whose two counts differ, or whose smaller min |pivot| is below
+ * pivot_guard * ||A||_inf, is factorized again in FP64 at mu.  All of it runs
+ * on the device.  min_abs_pivot of a certified shift is the smaller of its two
+ * mixed values.  h2_info counts the shifts checked and re-run.
  */
 int h2_inertia(h2_handle h, const double* shifts, int64_t ns, int64_t* counts,
                double* min_abs_pivot);
@@ -158,8 +174,9 @@ int h2_inertia(h2_handle h, const double* shifts, int64_t ns, int64_t* counts,
 /*
  * h2_inertia_device -- as h2_inertia with DEVICE pointers; enqueued on the
  * handle's stream and returns without waiting (ns <= max_lanes).  In
- * H2_PREC_MIXED it returns the mixed counts without the FP64 re-run: the
- * caller applies the guard with the returned min |pivot|.
+ * H2_PREC_MIXED the certified counts of h2_inertia, with the pair batches
+ * (max_lanes / 2 shifts each) and the FP64 re-run batch all enqueued on the
+ * stream (a one-lane handle runs every shift in FP64).
  */
 int h2_inertia_device(h2_handle h, const double* d_shifts, int64_t ns, int64_t* d_counts,
                       double* d_min_abs_pivot);
@@ -220,8 +237,10 @@ int h2_group_create(const h2_handle* hs, int nh, h2_group* out);
  *   ns              : host, nh ints in 0..max_lanes, the shifts of each handle.
  *   d_counts        : device, nh * max_lanes int64, same layout (caller-owned).
  *   d_min_abs_pivot : device, same layout FP64, or NULL.
- * H2_PREC_MIXED handles return their mixed counts without the FP64 re-run,
- * as h2_inertia_device does.  Errors: H2_ERR_INVALID_ARG, H2_ERR_CUDA.
+ * H2_PREC_MIXED handles return certified counts as h2_inertia_device does:
+ * group batches of (mu - Delta, mu + Delta) pairs, then one FP64 group batch
+ * of every handle's uncertified shifts.  Errors: H2_ERR_INVALID_ARG,
+ * H2_ERR_CUDA.
  */
 int h2_group_inertia_device(h2_group g, const double* d_shifts, const int* ns, int64_t* d_counts,
                             double* d_min_abs_pivot);
@@ -242,8 +261,10 @@ void h2_group_destroy(h2_group g);
  * over the distinct active intervals, the first max_lanes of them in k order
  * (any number of k, in any order, repeats allowed: up to all n eigenvalues in
  * one call).  The intervals stay on the device.
- * H2_PREC_MIXED: mixed rounds (guarded as in h2_inertia) run while the
- * brackets are wider than Delta = 64 * 2^-24 * ||A||_inf; every bracket is
+ * H2_PREC_MIXED: mixed rounds (one mixed factorization per shift, no per-shift
+ * certificate) run while the brackets are wider than Delta = 64 * 2^-24 *
+ * ||A||_inf: a wrong mixed count at mu means an eigenvalue within ||E|| of
+ * mu, so it moves a bracket end by less than Delta.  Every bracket is
  * then widened by Delta and checked in FP64 (nu(lo) < k <= nu(hi), else it
  * restarts from the Gershgorin interval), and FP64 rounds finish to tol.
  *   k         : host, nk int64, 1-based, each in 1..n.
@@ -298,8 +319,20 @@ typedef struct {
     int last_rounds;         /* bisection rounds of the last h2_kth_eig */
     int64_t last_shifts;     /* shifts evaluated by the last h2_kth_eig */
     int last_mixed_rounds;   /* of those rounds, the mixed-precision ones */
-    int64_t last_guarded;    /* shifts re-run in FP64 by the last h2_inertia/h2_kth_eig */
+    int64_t guard_reruns;    /* mixed precision: shifts the guard of h2_inertia,
+                                h2_inertia_device and group batches re-ran in
+                                FP64, total since the build (waits for the
+                                handle's stream) */
     int64_t bracket_resets;  /* mixed brackets that failed their FP64 check (total) */
+    int cap_bound;           /* clusters (all levels) whose pivoted QR stopped at
+                                the rank cap with the sketch remainder still above
+                                trunc_tol: the cap, not eps_h2, set their rank */
+    double max_residual;     /* largest Frobenius norm of a sketch remainder left
+                                out by the truncation (<= trunc_tol where the
+                                tolerance, not the cap, stopped the QR) */
+    int64_t guard_checked;   /* mixed precision: shifts the guard checked, total
+                                since the build (guard_reruns / guard_checked =
+                                re-run rate) */
 } h2_stats;
 
 int h2_info(h2_handle h, h2_stats* out);
@@ -332,11 +365,11 @@ int h2_profile_batch(h2_handle h, const double* d_shifts, int64_t ns, int64_t* d
  * (the same kernel routine the H^2 factorization uses for its diagonal
  * blocks), and min_abs_pivot[i] as in h2_inertia, WITHOUT allocating any
  * memory.  The paper has no counterpart to this entry point.  It is for
- * callers that cannot call cudaMalloc: code that records a CUDA graph (an
- * allocation is not allowed while a stream is being captured), code that must
- * not add the device-wide synchronization an allocation can cause (for
- * example inside a latency-critical serving loop), and code that runs under a
- * fixed, pre-reserved memory budget.
+ * callers that cannot call cudaMalloc: code that runs under a fixed device
+ * memory budget reserved up front (an allocator owned by another framework
+ * or a pre-sized pool), and code that must not add the device-wide
+ * synchronization an allocation can cause (for example inside a
+ * latency-critical serving loop).
  *   d_A             : device, n x n row-major FP64, leading dimension lda >= n;
  *                     only read; the full matrix is read and must be symmetric.
  *   d_shifts        : device, ns FP64.
@@ -349,15 +382,76 @@ int h2_profile_batch(h2_handle h, const double* d_shifts, int64_t ns, int64_t* d
  * H2_ERR_INVALID_ARG, touching nothing, when that exceeds the maximum or when
  * n < 1, n > 1024, ns < 1, ns > 1024 or lda < n.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call shares
- * the array: calls that overlap on the GPU (on different streams or from
- * different threads) race and give wrong results.  Each call overwrites every
- * scratch element it reads, so nothing needs clearing between calls.
+ * current, and later calls reuse it; make that first call before any stream
+ * capture.  cudaDeviceReset on a device unloads the library's device code and
+ * leaves that stored address stale: do not call this entry point on a device
+ * after resetting it in the same process.  Every call shares the array: calls
+ * that overlap on the GPU (on different streams or from different threads)
+ * race and give wrong results.  Each call overwrites every scratch element it
+ * reads, so nothing needs clearing between calls.
  * Asynchronous: returns once the kernel is enqueued.
  */
 #define H2_NOALLOC_MAX_DOUBLES 1048576
 int h2_dense_inertia_noalloc(const double* d_A, int n, int lda, const double* d_shifts, int ns,
                              int64_t* d_counts, double* d_min_abs_pivot, void* stream);
+
+/*
+ * h2_export -- copies one level of the resident H^2 representation (Sec. 3.1,
+ * Eqs. shared-bases, transfer-matrices, lr_skeleton, dense_skeleton) to host
+ * memory, for tests and inspection.  Every point index is in tree order
+ * (h2_tree_perm).  Set buf->level (0 = root .. L = leaves) and the array
+ * pointers; NULL arrays are skipped, so a first call with all of them NULL
+ * returns the sizes.  Out:
+ *   nc, dq     : clusters; leading dimension of each basis/transfer matrix;
+ *   nfar, rbmax: stored far pairs (c > d); leading dimension of a coupling;
+ *   nnear, dm  : stored leaf near pairs (c >= d, leaf level only, else 0);
+ *                leading dimension of a near block.
+ * Arrays (host, caller-owned):
+ *   offsets  [nc + 1] int64: cluster c holds tree positions offsets[c]..;
+ *   ranks    [nc] int: build rank r_c (skeleton size);
+ *   residuals[nc] double: Frobenius norm of the sketch remainder that the
+ *             truncation of c's basis left out;
+ *   colours  [nc] int: distance-2 colour (elimination order, colour-major);
+ *   Q        [nc][dq][dq] double, row-major: at the leaves the orthogonal
+ *             [U^S U^R] of each cluster (m_c x m_c, the first r_c columns
+ *             U^S); above, the transfer matrix of each cluster, rows = the
+ *             children's skeleton coordinates (r_c1 + r_c2), first r_c
+ *             columns the parent skeleton;
+ *   far_pairs[2 nfar] int (c, d) and C [nfar][rbmax][rbmax] double: the
+ *             coupling S_cd^SS = E_c^T A_cd E_d (r_c x r_d), E the expanded
+ *             skeleton bases; S_dc^SS is its transpose;
+ *   near_pairs[2 nnear] int (c, d) and B [nnear][dm][dm] double: the
+ *             transformed near block [U^S U^R]_c^T A_cd [U^S U^R]_d.
+ * Errors: H2_ERR_INVALID_ARG (level outside 0..L, null handle or buf),
+ * H2_ERR_CUDA.
+ */
+typedef struct {
+    int level;
+    int nc, dq, nfar, rbmax, nnear, dm;
+    int64_t* offsets;
+    int* ranks;
+    double* residuals;
+    int* colours;
+    double* Q;
+    int* far_pairs;
+    double* C;
+    int* near_pairs;
+    double* B;
+} h2_export_buf;
+int h2_export(h2_handle h, h2_export_buf* buf);
+
+/*
+ * h2_compression_error -- the compression error of the resident H^2 matrix,
+ * measured on the device: *err2 = ||A - A~||_2 and *norm2 = ||A||_2, each by
+ * `iters` steps of power iteration from one seeded start vector.  A~ x is the
+ * nested H^2 product (skeleton coordinates up through the transfer matrices,
+ * couplings, back down, plus the dense near blocks; Sec. 3.1), A x evaluates
+ * the kernel entries on the fly (O(n^2) per step).  North-star criterion:
+ * err2 / norm2 <= 1e-8.  Power iteration approaches both norms from below.
+ * Blocks until done.  Errors: H2_ERR_INVALID_ARG (iters < 1, null pointers),
+ * H2_ERR_OOM, H2_ERR_CUDA.
+ */
+int h2_compression_error(h2_handle h, int iters, double* err2, double* norm2);
 
 /* tree order: perm[i] = index (0-based, in the input) of the i-th point in
  * tree order.  perm: host, caller-owned, n int64. */

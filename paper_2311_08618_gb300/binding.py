@@ -21,7 +21,7 @@ EXPORTED_SYMBOLS = ["h2_default_options", "h2_build", "h2_destroy", "h2_last_err
                     "h2_inertia_device", "h2_kth_eig", "h2_info", "h2_tree_perm", "h2_level_ranks",
                     "h2_profile_batch", "h2_dense_inertia_noalloc", "h2_status", "h2_heartbeat",
                     "h2_group_create", "h2_group_inertia_device", "h2_group_launches", "h2_group_destroy",
-                    "h2_autotune_choice", "h2_plan_summary"]
+                    "h2_autotune_choice", "h2_plan_summary", "h2_export", "h2_compression_error"]
 KIND_NAMES = ["init", "recomp", "rotate", "ldl", "trsm", "schur", "merge", "other"]
 
 
@@ -33,7 +33,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("admissibility", C.c_int), ("eps_h2", C.c_double),
                 ("fill_cap", C.c_int), ("sketch_cols", C.c_int), ("seed", C.c_uint64),
                 ("max_lanes", C.c_int), ("pivot_guard", C.c_double), ("stream", C.c_void_p),
-                ("graphs", C.c_int), ("recomp_cluster_cols", C.c_int), ("autotune", C.c_int)]
+                ("graphs", C.c_int), ("recomp_cluster_cols", C.c_int), ("autotune", C.c_int),
+                ("hbm_budget", C.c_size_t)]
 
 
 class Stats(C.Structure):
@@ -42,7 +43,15 @@ class Stats(C.Structure):
                 ("gershgorin_lo", C.c_double), ("gershgorin_hi", C.c_double), ("trunc_tol", C.c_double),
                 ("workspace_bytes", C.c_int64), ("lanes", C.c_int), ("kernels_per_batch", C.c_int),
                 ("last_rounds", C.c_int), ("last_shifts", C.c_int64), ("last_mixed_rounds", C.c_int),
-                ("last_guarded", C.c_int64), ("bracket_resets", C.c_int64)]
+                ("guard_reruns", C.c_int64), ("bracket_resets", C.c_int64), ("cap_bound", C.c_int),
+                ("max_residual", C.c_double), ("guard_checked", C.c_int64)]
+
+
+class ExportBuf(C.Structure):
+    _fields_ = [("level", C.c_int), ("nc", C.c_int), ("dq", C.c_int), ("nfar", C.c_int), ("rbmax", C.c_int),
+                ("nnear", C.c_int), ("dm", C.c_int), ("offsets", C.c_void_p), ("ranks", C.c_void_p),
+                ("residuals", C.c_void_p), ("colours", C.c_void_p), ("Q", C.c_void_p), ("far_pairs", C.c_void_p),
+                ("C", C.c_void_p), ("near_pairs", C.c_void_p), ("B", C.c_void_p)]
 
 
 class H2Error(RuntimeError):
@@ -99,6 +108,10 @@ def lib():
         L.h2_autotune_choice.restype = C.c_int
         L.h2_plan_summary.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_int, P, P, P, P]
         L.h2_plan_summary.restype = C.c_int
+        L.h2_export.argtypes = [P, C.POINTER(ExportBuf)]
+        L.h2_export.restype = C.c_int
+        L.h2_compression_error.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.h2_compression_error.restype = C.c_int
         for f in ("h2_build", "h2_inertia", "h2_inertia_device", "h2_kth_eig", "h2_info",
                   "h2_tree_perm", "h2_level_ranks", "h2_profile_batch"):
             getattr(L, f).restype = C.c_int
@@ -210,6 +223,30 @@ class H2Matrix:
         out = np.zeros(2, dtype=np.int32)
         _check(lib().h2_autotune_choice(self._h, int(level), out.ctypes.data_as(C.c_void_p)))
         return int(out[0]), int(out[1])
+
+    def h2_export(self, level):
+        """One level of the resident representation (see h2_export in the
+        header): dict with offsets, ranks, residuals, colours, Q [nc, dq, dq],
+        far_pairs [nfar, 2], C [nfar, rbmax, rbmax], near_pairs, B."""
+        b = ExportBuf()
+        b.level = int(level)
+        _check(lib().h2_export(self._h, C.byref(b)))
+        out = {"offsets": np.zeros(b.nc + 1, dtype=np.int64), "ranks": np.zeros(b.nc, dtype=np.int32),
+               "residuals": np.zeros(b.nc), "colours": np.zeros(b.nc, dtype=np.int32),
+               "Q": np.zeros((b.nc, b.dq, b.dq)), "far_pairs": np.zeros((b.nfar, 2), dtype=np.int32),
+               "C": np.zeros((b.nfar, b.rbmax, b.rbmax)), "near_pairs": np.zeros((b.nnear, 2), dtype=np.int32),
+               "B": np.zeros((b.nnear, b.dm, b.dm))}
+        for f in ("offsets", "ranks", "residuals", "colours", "Q", "far_pairs", "C", "near_pairs", "B"):
+            setattr(b, f, out[f].ctypes.data_as(C.c_void_p) if out[f].size else None)
+        _check(lib().h2_export(self._h, C.byref(b)))
+        return out
+
+    def h2_compression_error(self, iters=30):
+        """(||A - A~||_2, ||A||_2) by power iteration on the device."""
+        e = C.c_double()
+        a = C.c_double()
+        _check(lib().h2_compression_error(self._h, int(iters), C.byref(e), C.byref(a)))
+        return e.value, a.value
 
     def h2_level_ranks(self, level):
         r = np.zeros(1 << level, dtype=np.int32)

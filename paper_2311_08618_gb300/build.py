@@ -22,7 +22,7 @@ def _nvcc():
 
 
 def _sources():
-    cu = ["h2_build.cu", "h2_factor.cu", "h2_noalloc.cu"]
+    cu = ["h2_build.cu", "h2_factor.cu", "h2_noalloc.cu", "h2_matvec.cu"]
     cpp = ["h2_plan.cpp", "h2_api.cpp"]
     return [os.path.join(CSRC, f) for f in cu], [os.path.join(CSRC, f) for f in cpp]
 

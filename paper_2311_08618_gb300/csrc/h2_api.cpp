@@ -1,6 +1,7 @@
 // C ABI entry points (include/h2eig.h): argument checks, error reporting and
 // handle lifetime.  All arithmetic runs in the CUDA kernels of h2_build.cu and
 // h2_factor.cu.
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -58,7 +59,8 @@ int h2_build(const double* points, int64_t n, int d, h2_kernel kernel, int leaf,
     h2_options o;
     h2_default_options(&o);
     if (opt) o = *opt;
-    if (o.max_lanes <= 0) o.max_lanes = 64;
+    if (o.max_lanes > 65535) { set_error("h2_build: max_lanes above 65535"); return H2_ERR_INVALID_ARG; }
+    if (o.max_lanes <= 0) o.max_lanes = o.hbm_budget > 0 ? 65535 : 64;
     if (!(o.pivot_guard > 0.0)) o.pivot_guard = 1e-4;
     if (!(o.eps_h2 >= 0.0) || o.fill_cap < 0 || o.sketch_cols < 0 ||
         (o.precision != H2_PREC_FP64 && o.precision != H2_PREC_MIXED && o.precision != H2_PREC_FP64_TC) ||
@@ -93,7 +95,17 @@ int h2_build(const double* points, int64_t n, int d, h2_kernel kernel, int leaf,
     }
     h->plan = make_plan(points, n, d, leaf, eta, o.admissibility);
     int rc = build_device(h);
-    if (rc == H2_OK) rc = alloc_workspace(h, o.max_lanes);
+    if (rc == H2_OK && o.hbm_budget > 0) {
+        const size_t per = workspace_lane_bytes(h);
+        const size_t fit = per > 0 ? o.hbm_budget / per : 0;
+        if (fit < 1) {
+            set_error("h2_build: one lane's workspace (" + std::to_string(per) + " bytes) exceeds hbm_budget");
+            rc = H2_ERR_OOM;
+        } else {
+            h->opt.max_lanes = (int)std::min<size_t>((size_t)o.max_lanes, fit);
+        }
+    }
+    if (rc == H2_OK) rc = alloc_workspace(h, h->opt.max_lanes);
     if (rc != H2_OK) {
         std::string keep = g_last_error;
         free_device(h);
@@ -228,9 +240,30 @@ int h2_info(h2_handle h, h2_stats* s) {
     s->last_rounds = h->last_rounds;
     s->last_shifts = h->last_shifts;
     s->last_mixed_rounds = h->last_mixed_rounds;
-    s->last_guarded = h->last_guarded;
+    int64_t checked = 0, reruns = 0;
+    int rc = guard_tally(h, &checked, &reruns);
+    if (rc) return rc;
+    s->guard_reruns = reruns;
+    s->guard_checked = checked;
     s->bracket_resets = h->last_bracket_resets;
+    for (const auto& D : h->lev)
+        for (double r : D.resid) {
+            s->cap_bound += r > h->tol ? 1 : 0;
+            s->max_residual = std::max(s->max_residual, r);
+        }
     return H2_OK;
+}
+
+int h2_export(h2_handle h, h2_export_buf* buf) {
+    g_last_error.clear();
+    if (!h || !buf) { set_error("h2_export: null pointer"); return H2_ERR_INVALID_ARG; }
+    return run_export(h, buf);
+}
+
+int h2_compression_error(h2_handle h, int iters, double* err2, double* norm2) {
+    g_last_error.clear();
+    if (!h || !err2 || !norm2 || iters < 1) { set_error("h2_compression_error: bad arguments"); return H2_ERR_INVALID_ARG; }
+    return run_compression_error(h, iters, err2, norm2);
 }
 
 int h2_profile_batch(h2_handle h, const double* d_shifts, int64_t ns, int64_t* d_counts, double* ms,

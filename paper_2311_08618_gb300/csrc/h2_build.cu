@@ -147,7 +147,7 @@ __global__ void k_sum_levels(const double* Z, const int64_t* leaf_off, int L, in
 // grid: clusters of the level.  scratch per cluster: Yhat (dq x s), V (dq x dq).
 __global__ void k_basis(const double* Ylev, int s, const int64_t* off, int leaf_level,
                         const double* Echild, int rbc, const int* rb_child, int dq, double tol,
-                        int cap, double* scratch, double* Qout, int* rank_out) {
+                        int cap, double* scratch, double* Qout, int* rank_out, double* resid_out) {
     int c = blockIdx.x;
     __shared__ double red[32];
     __shared__ int redi[32];
@@ -176,9 +176,21 @@ __global__ void k_basis(const double* Ylev, int s, const int64_t* off, int leaf_
     }
     __syncthreads();
     int k = cta_pivqr<NT>(Yh, s, m, s, tol, cap, V, dq, red, redi);
+    // Frobenius norm of what the truncation left out: after k reflections the
+    // not-yet-pivoted remainder of the sketch sits in Yh[k:m, k:s]; it is
+    // <= tol unless the rank cap stopped the QR first
+    double rem = 0.0;
+    for (int e = threadIdx.x; e < (m - k) * (s - k); e += NT) {
+        const double y = Yh[(size_t)(k + e / (s - k)) * s + k + e % (s - k)];
+        rem += y * y;
+    }
+    rem = block_sum<NT>(rem, red);
     double* Q = Qout + (size_t)c * dq * dq;
     cta_form_q<NT>(Q, dq, m, V, dq, k);
-    if (threadIdx.x == 0) rank_out[c] = k;
+    if (threadIdx.x == 0) {
+        rank_out[c] = k;
+        resid_out[c] = sqrt(rem);
+    }
 }
 
 // E at this level (n x rbl, tree order rows): leaf E = Q[:, :r]; upper
@@ -381,13 +393,18 @@ int build_device(h2_matrix* h) {
         if ((rc = dalloc(&d_scr, (size_t)D.nc * ((size_t)D.dq * s + (size_t)D.dq * D.dq)))) return rc;
         if ((rc = dalloc(&D.d_Q, (size_t)D.nc * D.dq * D.dq))) return rc;
         if ((rc = dalloc(&D.d_rb, D.nc))) return rc;
+        double* d_res;
+        if ((rc = dalloc(&d_res, D.nc))) return rc;
         k_basis<<<D.nc, NT, 0, st>>>(d_Y, s, d_off, leaf_level,
                                                        leaf_level ? nullptr : d_E[l + 1], rbc,
                                                        leaf_level ? nullptr : h->lev[l + 1].d_rb, D.dq,
-                                                       h->tol, cap, d_scr, D.d_Q, D.d_rb);
+                                                       h->tol, cap, d_scr, D.d_Q, D.d_rb, d_res);
         D.rb.resize(D.nc);
+        D.resid.resize(D.nc);
         CK(cudaMemcpyAsync(D.rb.data(), D.d_rb, D.nc * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(D.resid.data(), d_res, D.nc * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        cudaFree(d_res);
         D.rbmax = 0;
         for (int c = 0; c < D.nc; ++c) D.rbmax = std::max(D.rbmax, D.rb[c]);
         h->max_rank = std::max(h->max_rank, D.rbmax);

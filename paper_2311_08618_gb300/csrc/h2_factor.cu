@@ -2017,6 +2017,105 @@ __global__ void k_finish(const unsigned long long* neg, const unsigned long long
     mp[lane] = __longlong_as_double((long long)minpiv[lane]);
 }
 
+// ---- mixed-precision guard: certified counts (Parlett's criterion, Sec. 4.1)
+// A mixed factorization of A~ - mu I is exact for A~ + E - mu I with ||E|| of
+// the order of the FP32 product rounding.  Its count can differ from nu(mu)
+// only if an eigenvalue lies within ||E|| of mu.  With Delta > 2 ||E||: if
+// the mixed counts at mu - Delta and mu + Delta agree (= c), then nu is
+// constant on [mu - Delta + ||E||, mu + Delta - ||E||], an interval around
+// mu, so nu(mu) = c.  Shifts whose pair disagrees, or whose min |pivot| is
+// below the benchmark spec's threshold, are factorized again in FP64.
+
+// lanes 2i and 2i + 1 of the next mixed batch: mu_i - Delta and mu_i + Delta
+__global__ void k_guard_pairs(const double* req, int nc, double delta, double* shifts, int* active) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *active = 2 * nc;
+    if (i < nc) {
+        shifts[2 * i] = req[i] - delta;
+        shifts[2 * i + 1] = req[i] + delta;
+    }
+}
+
+// Certifies shifts c0 .. c0 + nc - 1 from the pair counts of the batch just
+// run; the others are appended, in index order, to the FP64 list.  One CTA.
+// tally[0] += shifts checked, tally[1] += shifts sent to FP64.
+__global__ void __launch_bounds__(1024) k_guard_certify(const int64_t* cnt, const double* mp, int nc, int c0,
+                                                        double theta, int64_t* out_c, double* out_mp,
+                                                        int* rr_idx, int* rr_n, unsigned long long* tally) {
+    __shared__ int wsum[32];
+    __shared__ int s_base;
+    const int t = threadIdx.x, w = t >> 5, l = t & 31, nw = (blockDim.x + 31) >> 5;
+    if (t == 0) s_base = *rr_n;
+    __syncthreads();
+    for (int b0 = 0; b0 < nc; b0 += blockDim.x) {
+        const int i = b0 + t;
+        int f = 0;
+        if (i < nc) {
+            const int64_t a = cnt[2 * i], b = cnt[2 * i + 1];
+            const double m = fmin(mp[2 * i], mp[2 * i + 1]);
+            if (a == b && m >= theta) {
+                out_c[c0 + i] = a;
+                out_mp[c0 + i] = m;
+            } else {
+                f = 1;
+            }
+        }
+        int incl = f;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (l >= o) incl += v;
+        }
+        if (l == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            int v = l < nw ? wsum[l] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, v, o);
+                if (l >= o) v += u;
+            }
+            if (l < nw) wsum[l] = v;
+        }
+        __syncthreads();
+        if (f) rr_idx[s_base + (w > 0 ? wsum[w - 1] : 0) + incl - 1] = c0 + i;
+        __syncthreads();
+        if (t == 0) s_base += wsum[nw - 1];
+        __syncthreads();
+    }
+    if (t == 0) {
+        tally[1] += (unsigned long long)(s_base - *rr_n);
+        tally[0] += (unsigned long long)nc;
+        *rr_n = s_base;
+    }
+}
+
+// a one-lane handle cannot hold a pair: every shift goes to FP64
+__global__ void k_guard_all(int ns, int* rr_idx, int* rr_n, unsigned long long* tally) {
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) rr_idx[i] = i;
+    if (threadIdx.x == 0) {
+        *rr_n = ns;
+        tally[0] += (unsigned long long)ns;
+        tally[1] += (unsigned long long)ns;
+    }
+}
+
+// the FP64 batch: shifts of the list in lanes 0 .. rr_n - 1
+__global__ void k_guard_rerun_setup(const double* req, const int* rr_idx, const int* rr_n, double* shifts,
+                                    int* active) {
+    const int n = *rr_n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *active = n;
+    if (i < n) shifts[i] = req[rr_idx[i]];
+}
+
+__global__ void k_guard_scatter(const int* rr_idx, const int* rr_n, const int64_t* cnt, const double* mp,
+                                int64_t* out_c, double* out_mp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < *rr_n) {
+        out_c[rr_idx[i]] = cnt[i];
+        out_mp[rr_idx[i]] = mp[i];
+    }
+}
+
 // ------------------------------------------------------------ workspace --
 constexpr size_t kSmemCap = 200 * 1024;   // dynamic shared memory staged per CTA at most
 constexpr size_t kSmemMax = 227 * 1024;   // opt-in limit per CTA
@@ -2050,6 +2149,13 @@ struct FactorState {
     int* d_nact = nullptr;
     int* d_first = nullptr;   // [lanes]: the intervals of a round
     int nk_cap = 0;
+    // mixed-precision guard: requested shifts, certified results, FP64 list
+    double* d_req = nullptr;      // [lanes]
+    int64_t* d_gc = nullptr;      // [lanes]
+    double* d_gmp = nullptr;      // [lanes]
+    int* d_rr_idx = nullptr;      // [lanes]
+    int* d_rr_n = nullptr;        // [1]
+    unsigned long long* d_tally = nullptr;   // [2]: shifts checked, shifts re-run in FP64
 };
 
 static FactorState* state_of(h2_matrix* h) {
@@ -2058,6 +2164,10 @@ static FactorState* state_of(h2_matrix* h) {
 
 static int ensure_graph(h2_matrix* h, int mixed);
 static int autotune(h2_matrix* h);
+static void guard_pairs(h2_matrix* h, int c0, int nc);
+static void guard_certify(h2_matrix* h, int c0, int nc);
+static void guard_rerun_setup(h2_matrix* h);
+static void guard_scatter(h2_matrix* h);
 // graphs unless the handle asks for plain launches or the environment
 // variable H2_NO_GRAPH=1 (a diagnostic) turns them off for the process
 static bool use_graphs(const h2_matrix* h) {
@@ -2069,19 +2179,12 @@ static bool use_graphs(const h2_matrix* h) {
 }
 int heartbeat_setup();
 
-int alloc_workspace(h2_matrix* h, int lanes) {
-    int hrc = heartbeat_setup();
-    if (hrc) return hrc;
-    const Plan& P = h->plan;
-    const int L = P.L;
-    Workspace& ws = h->ws;
-    ws.lanes = lanes;
-    auto* fs = new FactorState();
-    ws.graph_state = fs;
-    fs->lw.resize(L + 1);
-    int fill_cap = h->opt.fill_cap > 0 ? h->opt.fill_cap : 2 * h->rank;
+// padded block dimension of every level (leaves: the largest leaf; above:
+// twice the children's skeleton cap)
+static int set_level_dims(h2_matrix* h) {
+    const int L = h->plan.L;
+    const int fill_cap = h->opt.fill_cap > 0 ? h->opt.fill_cap : 2 * h->rank;
     h->fill_cap_eff = fill_cap;
-    // padded dims per level
     for (int l = L; l >= 0; --l) {
         LevelDev& D = h->lev[l];
         if (l == L) D.dmax = std::max(1, h->mmax);
@@ -2095,6 +2198,66 @@ int alloc_workspace(h2_matrix* h, int lanes) {
             return H2_ERR_INVALID_ARG;
         }
     }
+    return H2_OK;
+}
+
+// largest near count, near-or-fill count and fill count of a cluster of level l
+static void level_maxima(const LevelPlan& lp, int* ntarg_max, int* nrow_max, int* nfill_max) {
+    *ntarg_max = *nrow_max = *nfill_max = 1;
+    for (int p = 0; p < lp.nc; ++p) {
+        int nn = 0, nf = 0;
+        for (int x = 0; x < lp.nc; ++x) {
+            nn += lp.is_near(p, x);
+            nf += lp.is_fill(p, x);
+        }
+        *ntarg_max = std::max(*ntarg_max, nn);
+        *nrow_max = std::max(*nrow_max, nn + nf);
+        *nfill_max = std::max(*nfill_max, nf);
+    }
+}
+
+// Device bytes of the workspace per lane (every buffer of alloc_workspace
+// grows linearly with the lanes; the work lists do not depend on them).
+size_t workspace_lane_bytes(h2_matrix* h) {
+    if (set_level_dims(h)) return 0;
+    const Plan& P = h->plan;
+    size_t slots = 0, scratch = 0, merge = 0;
+    for (int l = 0; l <= P.L; ++l) {
+        const LevelDev& D = h->lev[l];
+        const LevelPlan& lp = P.lev[l];
+        int nt, nr, nf;
+        level_maxima(lp, &nt, &nr, &nf);
+        const ScratchLayout lay = scratch_layout(D.dmax, nf, nt, h->opt.precision == H2_PREC_FP64_TC);
+        size_t ncl_max = 0;
+        for (const auto& cl : lp.color_lists) ncl_max = std::max(ncl_max, cl.size());
+        slots += (size_t)std::max(D.nslots, 1) * D.dmax * D.dmax * 8 + (size_t)D.nc * 8;
+        scratch = std::max(scratch, ncl_max * lay.total * 8);
+        if (l < P.L) merge = std::max(merge, (size_t)D.nslots * 2 * D.dmax * D.dmax * 8);
+    }
+    return slots + scratch + merge + 5 * 8;
+}
+
+int alloc_workspace(h2_matrix* h, int lanes) {
+    int hrc = heartbeat_setup();
+    if (hrc) return hrc;
+    const Plan& P = h->plan;
+    const int L = P.L;
+    Workspace& ws = h->ws;
+    ws.lanes = lanes;
+    auto* fs = new FactorState();
+    ws.graph_state = fs;
+    fs->lw.resize(L + 1);
+    if ((hrc = set_level_dims(h))) return hrc;
+    {   // admission by footprint: fail before allocating when the workspace cannot fit
+        const size_t need = workspace_lane_bytes(h) * (size_t)lanes;
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        if (need > free_b) {
+            set_error("workspace of " + std::to_string(lanes) + " lanes needs " + std::to_string(need) +
+                      " bytes, " + std::to_string(free_b) + " free on the device");
+            return H2_ERR_OOM;
+        }
+    }
     size_t scratch_max = 0, merge_max = 0;
     int rc;
     for (int l = 0; l <= L; ++l) {
@@ -2102,17 +2265,8 @@ int alloc_workspace(h2_matrix* h, int lanes) {
         const LevelPlan& lp = P.lev[l];
         LevelWork& W = fs->lw[l];
         int nc = lp.nc;
-        int ntarg_max = 1, nrow_max = 1, nfill_max = 1;
-        for (int p = 0; p < nc; ++p) {
-            int nn = 0, nf = 0;
-            for (int x = 0; x < nc; ++x) {
-                nn += lp.is_near(p, x);
-                nf += lp.is_fill(p, x);
-            }
-            ntarg_max = std::max(ntarg_max, nn);
-            nrow_max = std::max(nrow_max, nn + nf);
-            nfill_max = std::max(nfill_max, nf);
-        }
+        int ntarg_max, nrow_max, nfill_max;
+        level_maxima(lp, &ntarg_max, &nrow_max, &nfill_max);
         W.lay = scratch_layout(D.dmax, nfill_max, ntarg_max, h->opt.precision == H2_PREC_FP64_TC);
         for (const auto& cl : lp.color_lists) W.ncl_max = std::max<int>(W.ncl_max, (int)cl.size());
         scratch_max = std::max(scratch_max, (size_t)W.ncl_max * lanes * W.lay.total);
@@ -2211,8 +2365,11 @@ int alloc_workspace(h2_matrix* h, int lanes) {
     if ((rc = dalloc(&ws.d_neg, lanes)) || (rc = dalloc(&ws.d_minpiv, lanes)) || (rc = dalloc(&ws.d_err, 8)) ||
         (rc = dalloc(&ws.d_shifts, lanes)) || (rc = dalloc(&fs->d_active, 1)) ||
         (rc = dalloc(&fs->d_counts, lanes)) || (rc = dalloc(&fs->d_mp, lanes)) ||
-        (rc = dalloc(&fs->d_stats, 2 * H2_NKINDS)))
+        (rc = dalloc(&fs->d_stats, 2 * H2_NKINDS)) || (rc = dalloc(&fs->d_req, lanes)) ||
+        (rc = dalloc(&fs->d_gc, lanes)) || (rc = dalloc(&fs->d_gmp, lanes)) || (rc = dalloc(&fs->d_rr_idx, lanes)) ||
+        (rc = dalloc(&fs->d_rr_n, 1)) || (rc = dalloc(&fs->d_tally, 2)))
         return rc;
+    CK(cudaMemsetAsync(fs->d_tally, 0, 2 * sizeof(unsigned long long), h->stream));
     ws.bytes = bytes;
     CK(cudaMemsetAsync(ws.d_err, 0, 8 * sizeof(int), h->stream));
     // capture the batch graphs now, while nothing else runs on the device:
@@ -2594,10 +2751,12 @@ struct h2_group_set {
     std::vector<h2_matrix*> hs;
     cudaStream_t stream = nullptr;
     int lanes = 0, mixed = 0;
-    std::vector<std::vector<h2::LaunchRec>> recs;
-    std::vector<h2::GLaunch> launches;
+    std::vector<std::vector<h2::LaunchRec>> recs;     // per handle, batch precision
+    std::vector<std::vector<h2::LaunchRec>> recs64;   // mixed groups: the FP64 re-run batch
+    std::vector<h2::GLaunch> launches, launches64;
     std::vector<void*> dev;
     cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph64 = nullptr;
 };
 
 namespace h2 {
@@ -2676,42 +2835,25 @@ void group_destroy(h2_group_set* g) {
     if (!g) return;
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->graph) cudaGraphExecDestroy(g->graph);
+    if (g->graph64) cudaGraphExecDestroy(g->graph64);
     for (void* p : g->dev) cudaFree(p);
     delete g;
 }
 
-int group_create(h2_matrix* const* hs, int nh, h2_group_set** out) {
-    auto* g = new h2_group_set();
-    g->hs.assign(hs, hs + nh);
-    g->stream = hs[0]->stream;
-    g->lanes = hs[0]->ws.lanes;
-    g->mixed = hs[0]->opt.precision == H2_PREC_MIXED ? 1 : 0;
-    for (h2_matrix* h : g->hs)
-        if (h->ws.lanes != g->lanes || h->opt.precision != hs[0]->opt.precision) {
-            delete g;
-            set_error("h2_group_create: handles need equal max_lanes and precision");
-            return H2_ERR_INVALID_ARG;
-        }
-    CK(cudaFuncSetAttribute(k_rotate_fp64_g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
-    CK(cudaFuncSetAttribute(k_rotate_oz_g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
-    CK(cudaFuncSetAttribute(k_rotate_g<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
-    CK(cudaFuncSetAttribute(k_rotate_g<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
-    CK(cudaFuncSetAttribute(k_rotate_g<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
-    CK(cudaFuncSetAttribute(k_ldl_g<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
-    CK(cudaFuncSetAttribute(k_ldl_warp_g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
-    CK(cudaFuncSetAttribute(k_ldl_g<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
-    CK(cudaFuncSetAttribute(k_trsm_g<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
-    CK(cudaFuncSetAttribute(k_trsm_g<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
-    // records of every handle, ordered by (phase, step, colour, op, variant)
+// The grouped launches of one batch precision over all handles of g (records
+// of equal (phase, step, colour, op, variant) merged) and their CUDA graph.
+static int group_graph(h2_group_set* g, int mixed, std::vector<std::vector<LaunchRec>>& recs,
+                       std::vector<GLaunch>& launches, cudaGraphExec_t* ge) {
+    const int nh = (int)g->hs.size();
     struct Ref {
         const LaunchRec* r;
         int h;
     };
     std::vector<Ref> all;
-    g->recs.resize(nh);
-    for (int i = 0; i < nh; ++i) g->recs[i] = factor_records(g->hs[i], g->mixed);
+    recs.resize(nh);
+    for (int i = 0; i < nh; ++i) recs[i] = factor_records(g->hs[i], mixed);
     for (int i = 0; i < nh; ++i)
-        for (const LaunchRec& r : g->recs[i]) all.push_back(Ref{&r, i});
+        for (const LaunchRec& r : recs[i]) all.push_back(Ref{&r, i});
     auto key = [](const LaunchRec* r) {
         return std::make_tuple(r->phase, r->step, r->colour, r->op, r->variant);
     };
@@ -2738,11 +2880,8 @@ int group_create(h2_matrix* const* hs, int nh, h2_group_set** out) {
                 break;
             default: gl.tiny = items; break;
         }
-        if (rc) {
-            group_destroy(g);
-            return rc;
-        }
-        g->launches.push_back(gl);
+        if (rc) return rc;
+        launches.push_back(gl);
         i = j;
     }
     // one graph for the whole group batch
@@ -2750,10 +2889,41 @@ int group_create(h2_matrix* const* hs, int nh, h2_group_set** out) {
     cudaGraph_t graph;
     CK(cudaStreamSynchronize(st));
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    for (const GLaunch& gl : g->launches) launch_grouped(gl, st);
+    for (const GLaunch& gl : launches) launch_grouped(gl, st);
     CK(cudaStreamEndCapture(st, &graph));
-    CK(cudaGraphInstantiate(&g->graph, graph, 0));
+    CK(cudaGraphInstantiate(ge, graph, 0));
     cudaGraphDestroy(graph);
+    return H2_OK;
+}
+
+int group_create(h2_matrix* const* hs, int nh, h2_group_set** out) {
+    auto* g = new h2_group_set();
+    g->hs.assign(hs, hs + nh);
+    g->stream = hs[0]->stream;
+    g->lanes = hs[0]->ws.lanes;
+    g->mixed = hs[0]->opt.precision == H2_PREC_MIXED ? 1 : 0;
+    for (h2_matrix* h : g->hs)
+        if (h->ws.lanes != g->lanes || h->opt.precision != hs[0]->opt.precision) {
+            delete g;
+            set_error("h2_group_create: handles need equal max_lanes and precision");
+            return H2_ERR_INVALID_ARG;
+        }
+    CK(cudaFuncSetAttribute(k_rotate_fp64_g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_rotate_oz_g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_rotate_g<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_rotate_g<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_rotate_g<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_ldl_g<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_ldl_warp_g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
+    CK(cudaFuncSetAttribute(k_ldl_g<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_trsm_g<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_trsm_g<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    int rc = group_graph(g, g->mixed, g->recs, g->launches, &g->graph);
+    if (rc == H2_OK && g->mixed) rc = group_graph(g, 0, g->recs64, g->launches64, &g->graph64);
+    if (rc) {
+        group_destroy(g);
+        return rc;
+    }
     *out = g;
     return H2_OK;
 }
@@ -2772,6 +2942,56 @@ int group_inertia(h2_group_set* g, const double* d_shifts, const int* ns, int64_
             set_error("h2_group_inertia_device: ns outside 0..max_lanes");
             return H2_ERR_INVALID_ARG;
         }
+    if (g->mixed) {
+        // certified counts (k_guard_certify): mixed group batches of
+        // (mu - Delta, mu + Delta) pairs, then one FP64 group batch of the
+        // shifts left uncertified, all handles together, no host round trip
+        int nsmax = 0;
+        for (int i = 0; i < nh; ++i) {
+            h2_matrix* h = g->hs[i];
+            FactorState* fs = state_of(h);
+            nsmax = std::max(nsmax, ns[i]);
+            if (ns[i] > 0)
+                CK(cudaMemcpyAsync(fs->d_req, d_shifts + (size_t)i * LN, ns[i] * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st));
+            k_set_int<<<1, 1, 0, st>>>(fs->d_rr_n, 0);
+        }
+        const int half = LN / 2;
+        if (half < 1) {
+            for (int i = 0; i < nh; ++i) {
+                FactorState* fs = state_of(g->hs[i]);
+                k_guard_all<<<1, 256, 0, st>>>(ns[i], fs->d_rr_idx, fs->d_rr_n, fs->d_tally);
+            }
+        } else {
+            for (int c0 = 0; c0 < nsmax; c0 += half) {
+                for (int i = 0; i < nh; ++i) {
+                    const int nc = std::max(0, std::min(half, ns[i] - c0));
+                    if (nc > 0) guard_pairs(g->hs[i], c0, nc);
+                    else k_set_int<<<1, 1, 0, st>>>(state_of(g->hs[i])->d_active, 0);
+                }
+                CK(cudaGraphLaunch(g->graph, st));
+                for (int i = 0; i < nh; ++i) {
+                    const int nc = std::max(0, std::min(half, ns[i] - c0));
+                    if (nc > 0) guard_certify(g->hs[i], c0, nc);
+                }
+            }
+        }
+        for (int i = 0; i < nh; ++i) guard_rerun_setup(g->hs[i]);
+        CK(cudaGraphLaunch(g->graph64, st));
+        for (int i = 0; i < nh; ++i) {
+            if (ns[i] == 0) continue;
+            h2_matrix* h = g->hs[i];
+            FactorState* fs = state_of(h);
+            guard_scatter(h);
+            CK(cudaMemcpyAsync(d_counts + (size_t)i * LN, fs->d_gc, ns[i] * sizeof(int64_t),
+                               cudaMemcpyDeviceToDevice, st));
+            if (d_minpiv)
+                CK(cudaMemcpyAsync(d_minpiv + (size_t)i * LN, fs->d_gmp, ns[i] * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st));
+        }
+        CK(cudaGetLastError());
+        return H2_OK;
+    }
     for (int i = 0; i < nh; ++i) {
         h2_matrix* h = g->hs[i];
         if (ns[i] > 0)
@@ -2821,6 +3041,62 @@ static int launch_batch(h2_matrix* h, int mixed) {
     return H2_OK;
 }
 
+// Delta of the mixed-precision guard: 64 u_32 ||A||_inf, about 200 times the
+// measured ||E|| of the FP32 products at n = 1024
+static double guard_delta(const h2_matrix* h) { return 64.0 * 0x1.0p-24 * h->norm_inf; }
+
+// Guard steps of one handle (see k_guard_certify).  Pairs of chunk c0 .. of
+// the shifts in fs->d_req, before the mixed batch of that chunk:
+static void guard_pairs(h2_matrix* h, int c0, int nc) {
+    FactorState* fs = state_of(h);
+    k_guard_pairs<<<(nc + 255) / 256, 256, 0, h->stream>>>(fs->d_req + c0, nc, guard_delta(h), h->ws.d_shifts,
+                                                           fs->d_active);
+}
+static void guard_certify(h2_matrix* h, int c0, int nc) {
+    FactorState* fs = state_of(h);
+    k_guard_certify<<<1, 1024, 0, h->stream>>>(fs->d_counts, fs->d_mp, nc, c0, h->opt.pivot_guard * h->norm_inf,
+                                               fs->d_gc, fs->d_gmp, fs->d_rr_idx, fs->d_rr_n, fs->d_tally);
+}
+static void guard_rerun_setup(h2_matrix* h) {
+    FactorState* fs = state_of(h);
+    const int LN = h->ws.lanes;
+    k_guard_rerun_setup<<<(LN + 255) / 256, 256, 0, h->stream>>>(fs->d_req, fs->d_rr_idx, fs->d_rr_n,
+                                                                 h->ws.d_shifts, fs->d_active);
+}
+static void guard_scatter(h2_matrix* h) {
+    FactorState* fs = state_of(h);
+    const int LN = h->ws.lanes;
+    k_guard_scatter<<<(LN + 255) / 256, 256, 0, h->stream>>>(fs->d_rr_idx, fs->d_rr_n, fs->d_counts, fs->d_mp,
+                                                             fs->d_gc, fs->d_gmp);
+}
+
+// Certified mixed-precision counts of the ns shifts in fs->d_req into
+// fs->d_gc / fs->d_gmp, all on the handle's stream: mixed batches of
+// (mu - Delta, mu + Delta) pairs, lanes / 2 shifts each, then one FP64 batch
+// of the shifts left uncertified.  No host round trip.
+static int enqueue_guarded(h2_matrix* h, int ns) {
+    FactorState* fs = state_of(h);
+    cudaStream_t st = h->stream;
+    const int half = h->ws.lanes / 2;
+    int rc;
+    k_set_int<<<1, 1, 0, st>>>(fs->d_rr_n, 0);
+    if (half < 1) {
+        k_guard_all<<<1, 256, 0, st>>>(ns, fs->d_rr_idx, fs->d_rr_n, fs->d_tally);
+    } else {
+        for (int c0 = 0; c0 < ns; c0 += half) {
+            const int nc = std::min(half, ns - c0);
+            guard_pairs(h, c0, nc);
+            if ((rc = launch_batch(h, 1))) return rc;
+            guard_certify(h, c0, nc);
+        }
+    }
+    guard_rerun_setup(h);
+    if ((rc = launch_batch(h, 0))) return rc;
+    guard_scatter(h);
+    CK(cudaGetLastError());
+    return H2_OK;
+}
+
 int run_inertia(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts, double* d_minpiv) {
     Workspace& ws = h->ws;
     FactorState* fs = state_of(h);
@@ -2830,13 +3106,30 @@ int run_inertia(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts,
         set_error("h2_inertia_device: ns exceeds max_lanes");
         return H2_ERR_INVALID_ARG;
     }
-    int rc = use_graphs(h) ? ensure_graph(h, h->opt.precision == H2_PREC_MIXED) : H2_OK;
+    const int mixed = h->opt.precision == H2_PREC_MIXED;
+    int rc = use_graphs(h) ? ensure_graph(h, mixed) : H2_OK;
     if (rc) return rc;
+    if (mixed) {
+        CK(cudaMemcpyAsync(fs->d_req, d_shifts, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if ((rc = enqueue_guarded(h, ns))) return rc;
+        CK(cudaMemcpyAsync(d_counts, fs->d_gc, ns * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+        if (d_minpiv) CK(cudaMemcpyAsync(d_minpiv, fs->d_gmp, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        return H2_OK;
+    }
     CK(cudaMemcpyAsync(ws.d_shifts, d_shifts, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
     k_set_int<<<1, 1, 0, st>>>(fs->d_active, ns);
-    if ((rc = launch_batch(h, h->opt.precision == H2_PREC_MIXED))) return rc;
+    if ((rc = launch_batch(h, 0))) return rc;
     CK(cudaMemcpyAsync(d_counts, fs->d_counts, ns * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
     if (d_minpiv) CK(cudaMemcpyAsync(d_minpiv, fs->d_mp, ns * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return H2_OK;
+}
+
+int guard_tally(h2_matrix* h, int64_t* checked, int64_t* rerun) {
+    unsigned long long t[2] = {0, 0};
+    CK(cudaMemcpyAsync(t, state_of(h)->d_tally, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *checked = (int64_t)t[0];
+    *rerun = (int64_t)t[1];
     return H2_OK;
 }
 
@@ -2901,24 +3194,23 @@ static int host_batch(h2_matrix* h, const double* shifts, int nb, int mixed, int
     return H2_OK;
 }
 
-// mixed precision guard: shifts of the batch whose min |pivot| is below
-// pivot_guard * ||A||_inf are factorized again in FP64 (counts and pivots
-// replaced).  Returns the number of shifts re-run.
-static int guard_rerun(h2_matrix* h, const double* shifts, int nb, int64_t* counts, double* minpiv, int* rerun) {
-    const double theta = h->opt.pivot_guard * h->norm_inf;
-    std::vector<int> idx;
-    for (int i = 0; i < nb; ++i)
-        if (!(minpiv[i] >= theta)) idx.push_back(i);
-    *rerun = (int)idx.size();
-    if (idx.empty()) return H2_OK;
-    std::vector<double> s2(idx.size()), m2(idx.size());
-    std::vector<int64_t> c2(idx.size());
-    for (size_t j = 0; j < idx.size(); ++j) s2[j] = shifts[idx[j]];
-    int rc = host_batch(h, s2.data(), (int)idx.size(), 0, c2.data(), m2.data());
+// mixed precision, host arrays: one batch of nb <= lanes shifts through the
+// certified device path (enqueue_guarded)
+static int host_batch_guarded(h2_matrix* h, const double* shifts, int nb, int64_t* counts, double* minpiv) {
+    Workspace& ws = h->ws;
+    FactorState* fs = state_of(h);
+    cudaStream_t st = h->stream;
+    CK(cudaMemcpyAsync(fs->d_req, shifts, nb * sizeof(double), cudaMemcpyHostToDevice, st));
+    int rc = enqueue_guarded(h, nb);
     if (rc) return rc;
-    for (size_t j = 0; j < idx.size(); ++j) {
-        counts[idx[j]] = c2[j];
-        minpiv[idx[j]] = m2[j];
+    CK(cudaMemcpyAsync(counts, fs->d_gc, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(minpiv, fs->d_gmp, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int err[8] = {0};
+    CK(cudaMemcpyAsync(err, ws.d_err, sizeof(err), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err[0]) {
+        set_error(err_message(err));
+        return H2_ERR_NUMERICAL;
     }
     return H2_OK;
 }
@@ -2967,16 +3259,11 @@ int run_inertia_host(h2_matrix* h, const double* shifts, int64_t ns, int64_t* co
     const int mixed = h->opt.precision == H2_PREC_MIXED;
     CK(cudaMemsetAsync(ws.d_err, 0, 8 * sizeof(int), st));
     std::vector<double> mp(ws.lanes);
-    h->last_guarded = 0;
     for (int64_t b0 = 0; b0 < ns; b0 += ws.lanes) {
         int nb = (int)std::min<int64_t>(ws.lanes, ns - b0);
-        int rc = host_batch(h, shifts + b0, nb, mixed, counts + b0, mp.data());
+        int rc = mixed ? host_batch_guarded(h, shifts + b0, nb, counts + b0, mp.data())
+                       : host_batch(h, shifts + b0, nb, 0, counts + b0, mp.data());
         if (rc) return rc;
-        if (mixed) {
-            int nre = 0;
-            if ((rc = guard_rerun(h, shifts + b0, nb, counts + b0, mp.data(), &nre))) return rc;
-            h->last_guarded += nre;
-        }
         if (minpiv) std::memcpy(minpiv + b0, mp.data(), nb * sizeof(double));
     }
     return H2_OK;
@@ -3063,12 +3350,11 @@ __global__ void k_bisect_update(double* lo, double* hi, const int64_t* kk, int n
 
 // One multisection round on the device-resident intervals: plan the shifts of
 // the distinct intervals wider than `width`, factorize them in the given
-// precision (mixed with guard: low-pivot shifts re-run in FP64) and narrow
-// every k.  h2_kth_eig runs its mixed rounds unguarded: a wrong mixed count
-// at mu implies |lambda_k - mu| < ||E|| << Delta, so the FP64 check of the
-// widened bracket certifies the result.
+// precision and narrow every k.  h2_kth_eig runs its mixed rounds without the
+// per-shift guard: a wrong mixed count at mu implies |lambda_k - mu| < ||E||
+// << Delta, so the FP64 check of the widened bracket certifies the result.
 // Returns the number of active intervals (0: nothing to do) in *nact.
-static int kth_round(h2_matrix* h, int nk, double width, int mixed, int guard, int* nact) {
+static int kth_round(h2_matrix* h, int nk, double width, int mixed, int* nact) {
     Workspace& ws = h->ws;
     FactorState* fs = state_of(h);
     cudaStream_t st = h->stream;
@@ -3081,22 +3367,6 @@ static int kth_round(h2_matrix* h, int nk, double width, int mixed, int guard, i
     if (*nact == 0) return H2_OK;
     int rc = launch_batch(h, mixed);
     if (rc) return rc;
-    if (mixed && guard) {
-        std::vector<double> sh(used), mp(used);
-        std::vector<int64_t> cnt(used);
-        CK(cudaMemcpyAsync(sh.data(), ws.d_shifts, used * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(cnt.data(), fs->d_counts, used * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(mp.data(), fs->d_mp, used * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        int nre = 0;
-        if ((rc = guard_rerun(h, sh.data(), used, cnt.data(), mp.data(), &nre))) return rc;
-        h->last_guarded += nre;
-        if (nre) {   // restore the round's shifts and the corrected counts
-            CK(cudaMemcpyAsync(ws.d_shifts, sh.data(), used * sizeof(double), cudaMemcpyHostToDevice, st));
-            CK(cudaMemcpyAsync(fs->d_counts, cnt.data(), used * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-            k_set_int<<<1, 1, 0, st>>>(fs->d_active, used);
-        }
-    }
     k_bisect_update<<<(unsigned)((nk + 127) / 128), 128, 0, st>>>(fs->d_lo, fs->d_hi, fs->d_k, nk, ws.d_shifts,
                                                                  fs->d_counts, fs->d_active);
     h->last_shifts += used;
@@ -3145,13 +3415,12 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
     int rounds = 0, nact = 0;
     h->last_rounds = 0;
     h->last_shifts = 0;
-    h->last_guarded = 0;
     h->last_mixed_rounds = 0;
     if (h->opt.precision == H2_PREC_MIXED) {
         // mixed rounds while the brackets are wider than Delta = 64 u_32 ||A||_inf
         const double delta = 64.0 * 0x1.0p-24 * h->norm_inf;
         while (true) {
-            if ((rc = kth_round(h, (int)nk, std::max(tol, delta), 1, 0, &nact))) return rc;
+            if ((rc = kth_round(h, (int)nk, std::max(tol, delta), 1, &nact))) return rc;
             if (nact == 0) break;
             ++rounds;
             ++h->last_mixed_rounds;
@@ -3196,7 +3465,7 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
     }
     // FP64 rounds to the requested width (Algorithm 1's stopping rule)
     while (true) {
-        if ((rc = kth_round(h, (int)nk, tol, 0, 0, &nact))) return rc;
+        if ((rc = kth_round(h, (int)nk, tol, 0, &nact))) return rc;
         if (nact == 0) break;
         ++rounds;
         if (rounds > 4096) { set_error("h2_kth_eig: bisection did not converge"); return H2_ERR_NUMERICAL; }
@@ -3242,6 +3511,8 @@ void free_workspace(h2_matrix* h) {
         }
         cudaFree(fs->d_active); cudaFree(fs->d_counts); cudaFree(fs->d_mp); cudaFree(fs->d_stats);
         cudaFree(fs->d_lo); cudaFree(fs->d_hi); cudaFree(fs->d_k); cudaFree(fs->d_nact); cudaFree(fs->d_first);
+        cudaFree(fs->d_req); cudaFree(fs->d_gc); cudaFree(fs->d_gmp); cudaFree(fs->d_rr_idx); cudaFree(fs->d_rr_n);
+        cudaFree(fs->d_tally);
         delete fs;
     }
     ws.graph_state = nullptr;

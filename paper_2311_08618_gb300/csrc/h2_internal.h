@@ -62,6 +62,7 @@ struct LevelDev {
     std::vector<int> far_of;       // nc*nc -> coupling id (for c > d), -1 otherwise
     std::vector<int> slot_a, slot_b;   // slot -> (c, d)
     std::vector<int> rb;           // build rank per cluster
+    std::vector<double> resid;     // Frobenius norm of the sketch remainder left out by the truncation
     // device arrays
     int* d_rb = nullptr;           // [nc]
     double* d_Q = nullptr;         // [nc][dq][dq] bases (leaf) / transfers (upper)
@@ -143,7 +144,6 @@ struct h2_matrix {
     int last_rounds = 0;           // bisection rounds of the last h2_kth_eig
     int64_t last_shifts = 0;       // shifts evaluated by the last h2_kth_eig
     int kernels_per_batch = 0;     // launches in one batch (graph nodes)
-    int64_t last_guarded = 0;      // mixed precision: shifts re-run in FP64 by the last call
     int last_mixed_rounds = 0;     // mixed rounds of the last h2_kth_eig
     int64_t last_bracket_resets = 0;  // brackets that failed the FP64 verification
 };
@@ -152,6 +152,7 @@ namespace h2 {
 void set_error(const std::string& msg);
 int build_device(h2_matrix* h);                         // construction kernels
 int alloc_workspace(h2_matrix* h, int lanes);
+size_t workspace_lane_bytes(h2_matrix* h);      // device bytes per lane
 int run_inertia(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts,
                 double* d_minpiv);                    // enqueue one batch
 int run_inertia_host(h2_matrix* h, const double* shifts, int64_t ns, int64_t* counts,
@@ -169,4 +170,7 @@ int group_launches(const h2_group_set* g);
 void group_destroy(h2_group_set* g);
 void heartbeat_read(unsigned int* out);
 void free_device(h2_matrix* h);
+int run_export(h2_matrix* h, h2_export_buf* buf);
+int guard_tally(h2_matrix* h, int64_t* checked, int64_t* rerun);   // mixed guard totals
+int run_compression_error(h2_matrix* h, int iters, double* err2, double* norm2);
 }  // namespace h2

@@ -36,11 +36,14 @@ __global__ void __launch_bounds__(NT) k_dense_inertia(const double* __restrict__
     const int s = blockIdx.x;
     double* S = scratch + (size_t)s * n * n;
     const double sg = shifts[s];
-    // ||A||_inf, for the exactly-zero pivot rule of the factorization
+    // ||A||_inf, for the exactly-zero pivot rule of the factorization: one
+    // warp per row, its lanes striding along the row (coalesced reads)
     double rmax = 0.0;
-    for (int i = threadIdx.x; i < n; i += NT) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < n; i += NT / 32) {
         double r = 0.0;
-        for (int j = 0; j < n; ++j) r += fabs(A[(size_t)i * lda + j]);
+        for (int j = lane; j < n; j += 32) r += fabs(A[(size_t)i * lda + j]);
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
         rmax = fmax(rmax, r);
     }
     double dummy;

@@ -1,6 +1,6 @@
 """h2_dense_inertia_noalloc, the entry point for callers that cannot allocate
-device memory (recording a CUDA graph, no device-wide synchronization allowed,
-fixed memory budget): called through the C ABI, its counts must equal those
+device memory (a fixed device memory budget reserved up front, or no
+device-wide synchronization allowed): called through the C ABI, its counts must equal those
 of h2_inertia (the allocating path) on the same small dense matrix, on two
 calls in a row that share the library's static scratch array.  Collected last
 on purpose (file name) so a stop-at-first-failure run has run every other test.
