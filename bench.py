@@ -548,6 +548,8 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
              "batched_fp64_over_plain": value / plain_rate,
              "batched_mixed_over_plain": precision["value"] / plain_rate}
     compression = _compression(args, X, dev, stream, e0, e1, d_sh, total, lanes) if args.compression else None
+    e2 = _e2_sweep(args) if args.e2_sweep and world == 1 else None
+    large = _large_configs(args) if args.large_configs and world == 1 else None
     serving_res = _serving(args) if args.serving_s > 0 and world == 1 else None
     batching_res = _batching(args) if args.batch_count > 0 and world == 1 else None
     ws_mb = info["workspace_bytes"] / 1e6
@@ -569,6 +571,7 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
                      "lambda": lam[0], "err_bound": lam[1]},
             "build_s": build_s, "roofline": roof, "clocks": clocks, "precision": precision,
             "all_eigs": all_eigs, "fp64_tc": fp64_tc, "plain_fp64": plain, "compression": compression,
+            "e2_sweep": e2, "large_configs": large,
             "serving": serving_res,
             "batching": batching_res}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -615,6 +618,93 @@ def _compression(args, X, dev, stream, e0, e1, d_sh, total, lanes):
                                      "fp64_shifts_per_s": args.steps * lanes / (ms / 1e3)}
         M.close()
     return out
+
+
+def _large_configs(args):
+    """The two large configurations at the lane counts one GB300 holds: the 3D
+    Yukawa n = 65536 matrix (leaf 256, rank 32) and the n = 262144 cylindrical
+    lattice (leaf 256, rank 48).  Per configuration: build time, workspace,
+    one timed batch in FP64_TC and in certified mixed precision after one
+    warm-up batch each, shifts at 10..90 % of the Gershgorin interval, and
+    whether the two precisions count alike."""
+    import torch
+    import paper_2311_08618_gb300 as pkg
+    out = {}
+    for name, lanes in (("yukawa3d_n65536", args.large_lanes_c2), ("cylinder_n262144", args.large_lanes_cyl)):
+        wl = WORKLOADS[name]
+        X = _points(wl)
+        st = torch.cuda.Stream()
+        rec = {"lanes": lanes}
+        counts = {}
+        for prec, key in ((pkg.H2_PREC_FP64_TC, "fp64_tc"), (pkg.H2_PREC_MIXED, "mixed")):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            M = pkg.H2Matrix(X, wl["kernel"], wl["kparams"], leaf=wl["leaf"], rank=wl["rank"], eta=wl["eta"],
+                             max_lanes=lanes, stream=st.cuda_stream, precision=prec)
+            torch.cuda.synchronize()
+            build_s = time.perf_counter() - t0
+            info = M.h2_info()
+            lo, hi = info["gershgorin_lo"], info["gershgorin_hi"]
+            sh = torch.tensor(lo + (hi - lo) * (0.1 + 0.8 * (np.arange(lanes) + 0.5) / lanes), dtype=torch.float64,
+                              device="cuda")
+            c = torch.zeros(lanes, dtype=torch.int64, device="cuda")
+            M.h2_inertia_device(sh, lanes, c)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            M.h2_inertia_device(sh, lanes, c)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            counts[key] = c.cpu().numpy().tolist()
+            rec[key] = {"build_s": build_s, "batch_s": ms / 1e3, "shifts_per_s": lanes / (ms / 1e3),
+                        "workspace_GB": info["workspace_bytes"] / 1e9, "max_rank": info["max_rank"],
+                        "levels": info["levels"], "near_pairs_leaf": info["near_pairs"],
+                        "fill_pairs_leaf": info["fill_pairs"]}
+            if prec == pkg.H2_PREC_MIXED:
+                g = M.h2_info()
+                rec[key]["guard_reruns"] = g["guard_reruns"]
+                rec[key]["guard_checked"] = g["guard_checked"]
+            M.close()
+            torch.cuda.empty_cache()
+        rec["counts"] = counts["fp64_tc"]
+        rec["counts_equal_fp64_tc_mixed"] = counts["fp64_tc"] == counts["mixed"]
+        out[name] = rec
+    return out
+
+
+def _e2_sweep(args):
+    """Sec. 5.1's second accuracy experiment: all n = 1024 eigenvalues of the
+    unit-circle Laplace matrix at decreasing eps_ev (eps_H2 = 1e-2 eps_ev,
+    leaf 64, rank cap 48); the largest error against the dense eigenvalues
+    (cuSOLVER eigvalsh in FP64 on the kernel matrix built with torch, a
+    reference outside the library's path) and ||A - A~||_2 from
+    h2_compression_error."""
+    import torch
+    import paper_2311_08618_gb300 as pkg
+    n = 1024
+    X = W.unit_circle(n, 5)
+    Xt = torch.tensor(X, dtype=torch.float64, device="cuda")
+    r = torch.cdist(Xt, Xt)
+    ev = torch.linalg.eigvalsh(1.0 / (r + 1e-3)).cpu().numpy()
+    del Xt, r
+    st = torch.cuda.Stream()
+    rows = []
+    for eps in (1e-2, 1e-4, 1e-6, 1e-8, 1e-10):
+        M = pkg.H2Matrix(X, W.LAPLACE_EPS, (1e-3, 0, 0, 0), leaf=64, rank=48, eta=1.0, eps_h2=1e-2 * eps,
+                         max_lanes=256, stream=st.cuda_stream)
+        err, nrm = M.h2_compression_error(40)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lam, eb = M.h2_kth_eig(np.arange(1, n + 1), eps)
+        sec = time.perf_counter() - t0
+        info = M.h2_info()
+        e = np.abs(lam - ev)
+        rows.append({"eps_ev": eps, "max_err": float(e.max()), "max_err_over_half_eps": float(e.max() / (0.5 * eps)),
+                     "below_half_eps": int(np.sum(e < 0.5 * eps)), "h2_err2": err, "max_rank": info["max_rank"],
+                     "seconds": sec, "rounds": info["last_rounds"], "shifts": info["last_shifts"]})
+        M.close()
+    return {"workload": "unit circle n=1024, 1/(r+1e-3), all 1024 eigenvalues, FP64, 256 lanes", "rows": rows}
 
 
 SERVING_SIZES = (1024, 2048, 4096, 8192)
@@ -786,6 +876,11 @@ def main():
     ap.add_argument("--batch-count", type=int, default=24, help="matrices of the batching sample (0: skip)")
     ap.add_argument("--all-eigs", type=int, default=1, help="1: also solve for all n eigenvalues (n <= 8192)")
     ap.add_argument("--compression", type=int, default=1, help="1: measure ||A - A~|| at rank caps r and r + 1")
+    ap.add_argument("--e2-sweep", type=int, default=1, help="1: all-eigenvalue error sweep over eps_ev (Sec. 5.1)")
+    ap.add_argument("--large-configs", type=int, default=1,
+                    help="1: one timed batch of the 3D n=65536 and the n=262144 cylinder configurations")
+    ap.add_argument("--large-lanes-c2", type=int, default=8)
+    ap.add_argument("--large-lanes-cyl", type=int, default=4)
     ap.add_argument("--circle-sweep", default="", help="comma-separated n: run the unit-circle scaling sweep only")
     ap.add_argument("--circle-lanes", type=int, default=4)
     ap.add_argument("--batch-nmax", type=int, default=8192)

@@ -277,6 +277,18 @@ int h2_kth_eig(h2_handle h, const int64_t* k, int64_t nk, double tol, double* ou
                double* err_bound);
 
 /*
+ * h2_kth_eig_in -- as h2_kth_eig, starting every bracket from the caller's
+ * interval [lo, hi] instead of the Gershgorin interval: the work unit of the
+ * parallel bisections of Sec. 4.2 (an interval known to hold a range of
+ * eigenvalue indices, e.g. from earlier inertia counts or a master's free
+ * list).  nu(lo) and nu(hi) are evaluated in FP64 first; every k must satisfy
+ * nu(lo) < k <= nu(hi), else H2_ERR_INTERVAL (the message gives both counts).
+ * Errors: as h2_kth_eig; H2_ERR_INVALID_ARG also for lo >= hi.
+ */
+int h2_kth_eig_in(h2_handle h, const int64_t* k, int64_t nk, double lo, double hi, double tol,
+                  double* out, double* err_bound);
+
+/*
  * h2_status -- waits for the handle's stream, then returns and clears the
  * device error record accumulated since the last h2_status or host-array call
  * (the asynchronous h2_inertia_device reports only here):

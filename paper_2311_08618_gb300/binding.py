@@ -21,7 +21,7 @@ EXPORTED_SYMBOLS = ["h2_default_options", "h2_build", "h2_destroy", "h2_last_err
                     "h2_inertia_device", "h2_kth_eig", "h2_info", "h2_tree_perm", "h2_level_ranks",
                     "h2_profile_batch", "h2_dense_inertia_noalloc", "h2_status", "h2_heartbeat",
                     "h2_group_create", "h2_group_inertia_device", "h2_group_launches", "h2_group_destroy",
-                    "h2_autotune_choice", "h2_plan_summary", "h2_export", "h2_compression_error"]
+                    "h2_autotune_choice", "h2_plan_summary", "h2_export", "h2_compression_error", "h2_kth_eig_in"]
 KIND_NAMES = ["init", "recomp", "rotate", "ldl", "trsm", "schur", "merge", "other"]
 
 
@@ -108,6 +108,8 @@ def lib():
         L.h2_autotune_choice.restype = C.c_int
         L.h2_plan_summary.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_int, P, P, P, P]
         L.h2_plan_summary.restype = C.c_int
+        L.h2_kth_eig_in.argtypes = [P, P, C.c_int64, C.c_double, C.c_double, C.c_double, P, P]
+        L.h2_kth_eig_in.restype = C.c_int
         L.h2_export.argtypes = [P, C.POINTER(ExportBuf)]
         L.h2_export.restype = C.c_int
         L.h2_compression_error.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -199,6 +201,15 @@ class H2Matrix:
         eb = np.zeros(k.size)
         _check(lib().h2_kth_eig(self._h, k.ctypes.data_as(C.c_void_p), k.size, float(tol),
                                 out.ctypes.data_as(C.c_void_p), eb.ctypes.data_as(C.c_void_p)))
+        return out, eb
+
+    def h2_kth_eig_in(self, ks, lo, hi, tol):
+        """h2_kth_eig with every bracket starting from [lo, hi]."""
+        k = np.ascontiguousarray(ks, dtype=np.int64).ravel()
+        out = np.zeros(k.size)
+        eb = np.zeros(k.size)
+        _check(lib().h2_kth_eig_in(self._h, k.ctypes.data_as(C.c_void_p), k.size, float(lo), float(hi), float(tol),
+                                   out.ctypes.data_as(C.c_void_p), eb.ctypes.data_as(C.c_void_p)))
         return out, eb
 
     def h2_info(self) -> dict:

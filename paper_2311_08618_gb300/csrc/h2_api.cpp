@@ -218,7 +218,21 @@ int h2_kth_eig(h2_handle h, const int64_t* k, int64_t nk, double tol, double* ou
     for (int64_t i = 0; i < nk; ++i)
         if (k[i] < 1 || k[i] > h->n) { set_error("h2_kth_eig: k out of 1..n"); return H2_ERR_INVALID_ARG; }
     if (nk == 0) return H2_OK;
-    return run_kth(h, k, nk, tol, out, err_bound);
+    return run_kth(h, k, nk, tol, out, err_bound, nullptr);
+}
+
+int h2_kth_eig_in(h2_handle h, const int64_t* k, int64_t nk, double lo, double hi, double tol, double* out,
+                  double* err_bound) {
+    g_last_error.clear();
+    if (!h || nk < 0 || (nk > 0 && (!k || !out)) || !(tol > 0.0) || !(lo < hi)) {
+        set_error("h2_kth_eig_in: bad arguments");
+        return H2_ERR_INVALID_ARG;
+    }
+    for (int64_t i = 0; i < nk; ++i)
+        if (k[i] < 1 || k[i] > h->n) { set_error("h2_kth_eig_in: k out of 1..n"); return H2_ERR_INVALID_ARG; }
+    if (nk == 0) return H2_OK;
+    const double iv[2] = {lo, hi};
+    return run_kth(h, k, nk, tol, out, err_bound, iv);
 }
 
 int h2_info(h2_handle h, h2_stats* s) {

@@ -2137,6 +2137,17 @@ struct LevelWork {
     int* d_far_of = nullptr;
 };
 
+// Parameters of the device-resident bisection loop (set before each launch of
+// its graph): the brackets in use and the width to reach; round statistics.
+struct KthLoop {
+    int nk;
+    double width;
+    int max_rounds;
+    int rounds;                 // rounds with work in this launch
+    unsigned long long shifts;  // shifts evaluated in this launch
+    int stopped;                // 1: the round cap ended the loop
+};
+
 struct FactorState {
     std::vector<LevelWork> lw;
     int* d_active = nullptr;
@@ -2156,6 +2167,10 @@ struct FactorState {
     int* d_rr_idx = nullptr;      // [lanes]
     int* d_rr_n = nullptr;        // [1]
     unsigned long long* d_tally = nullptr;   // [2]: shifts checked, shifts re-run in FP64
+    // device-resident bisection loop (graph with a conditional WHILE node)
+    KthLoop* d_loop = nullptr;
+    cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};   // [mixed]
+    int loop_nk_cap = 0;          // bracket capacity the loop graphs were built for
 };
 
 static FactorState* state_of(h2_matrix* h) {
@@ -3279,9 +3294,8 @@ int run_inertia_host(h2_matrix* h, const double* shifts, int64_t ns, int64_t* co
 // chunks (block prefix sums), keeps the first `lanes` distinct intervals
 // wider than tol in k order and spreads the lanes over them: interval u gets
 // q or q + 1 equally spaced interior points.
-__global__ void __launch_bounds__(1024) k_bisect_plan(const double* lo, const double* hi, int nk, double tol,
-                                                      int lanes, double* shifts, int* active, int* nact,
-                                                      int* first) {
+__device__ __forceinline__ void bisect_plan_body(const double* lo, const double* hi, int nk, double tol, int lanes,
+                                                 double* shifts, int* active, int* nact, int* first) {
     __shared__ int wsum[32];
     __shared__ int s_base;
     const int t = threadIdx.x, w = t >> 5, l = t & 31, nw = (blockDim.x + 31) >> 5;
@@ -3330,6 +3344,54 @@ __global__ void __launch_bounds__(1024) k_bisect_plan(const double* lo, const do
     }
 }
 
+__global__ void __launch_bounds__(1024) k_bisect_plan(const double* lo, const double* hi, int nk, double tol,
+                                                      int lanes, double* shifts, int* active, int* nact,
+                                                      int* first) {
+    bisect_plan_body(lo, hi, nk, tol, lanes, shifts, active, nact, first);
+}
+
+
+// The plan step of one loop iteration: as k_bisect_plan, then the loop's
+// condition -- continue while some interval is wider than the width and the
+// round cap is not reached (one thread sets it).
+__global__ void __launch_bounds__(1024) k_bisect_plan_loop(const double* lo, const double* hi, KthLoop* par,
+                                                           int lanes, double* shifts, int* active, int* nact,
+                                                           int* first, cudaGraphConditionalHandle cond) {
+    const int nk = par->nk;
+    bisect_plan_body(lo, hi, nk, par->width, lanes, shifts, active, nact, first);
+    if (threadIdx.x == 0) {
+        const int nd = *nact;
+        int go = nd > 0 ? 1 : 0;
+        if (go) {
+            par->rounds += 1;
+            par->shifts += (unsigned long long)lanes;
+            if (par->rounds >= par->max_rounds) {
+                par->stopped = 1;
+                go = 0;
+            }
+        }
+        cudaGraphSetConditional(cond, go);
+    }
+}
+
+__global__ void k_bisect_update_loop(double* lo, double* hi, const int64_t* kk, const KthLoop* par,
+                                     const double* shifts, const int64_t* counts, const int* active) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= par->nk) return;
+    double a = lo[k], b = hi[k];
+    const int64_t kv = kk[k];
+    const int ns = *active;
+    for (int i = 0; i < ns; ++i) {
+        const double mu = shifts[i];
+        if (a < mu && mu < b) {
+            if (counts[i] >= kv) b = mu;
+            else a = mu;
+        }
+    }
+    lo[k] = a;
+    hi[k] = b;
+}
+
 __global__ void k_bisect_update(double* lo, double* hi, const int64_t* kk, int nk, const double* shifts,
                                 const int64_t* counts, const int* active) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -3373,7 +3435,71 @@ static int kth_round(h2_matrix* h, int nk, double width, int mixed, int* nact) {
     return H2_OK;
 }
 
-int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out, double* err_bound) {
+// The whole bisection of one precision phase as one CUDA graph: a WHILE
+// conditional node whose body is plan (sets the condition), the batch's
+// kernels, and the bracket update.  The loop stops on the device when no
+// interval is wider than the width (or at the round cap), so a phase costs
+// one launch and one wait instead of one host round trip per round.
+static int build_loop_graph(h2_matrix* h, int mixed) {
+    Workspace& ws = h->ws;
+    FactorState* fs = state_of(h);
+    cudaStream_t st = h->stream;
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    k_bisect_plan_loop<<<1, 1024, 0, st>>>(fs->d_lo, fs->d_hi, fs->d_loop, ws.lanes, ws.d_shifts, fs->d_active,
+                                           fs->d_nact, fs->d_first, cond);
+    enqueue_factorization(h, st, nullptr, mixed);
+    k_bisect_update_loop<<<(unsigned)((fs->nk_cap + 127) / 128), 128, 0, st>>>(
+        fs->d_lo, fs->d_hi, fs->d_k, fs->d_loop, ws.d_shifts, fs->d_counts, fs->d_active);
+    cudaGraph_t captured;
+    CK(cudaStreamEndCapture(st, &captured));
+    CK(cudaGraphInstantiate(&fs->loop_exec[mixed], g, 0));
+    cudaGraphDestroy(g);
+    return H2_OK;
+}
+
+// runs bisection rounds on the device until every bracket is narrower than
+// `width`; adds the rounds and shifts to the handle's counters
+static int run_loop(h2_matrix* h, int nk, double width, int mixed, int* rounds) {
+    FactorState* fs = state_of(h);
+    cudaStream_t st = h->stream;
+    if (fs->loop_nk_cap != fs->nk_cap) {
+        for (auto& e : fs->loop_exec)
+            if (e) {
+                cudaGraphExecDestroy(e);
+                e = nullptr;
+            }
+        fs->loop_nk_cap = fs->nk_cap;
+    }
+    int rc;
+    if (!fs->loop_exec[mixed] && (rc = build_loop_graph(h, mixed))) return rc;
+    KthLoop par{nk, width, 4096, 0, 0ull, 0};
+    CK(cudaMemcpyAsync(fs->d_loop, &par, sizeof(par), cudaMemcpyHostToDevice, st));
+    CK(cudaGraphLaunch(fs->loop_exec[mixed], st));
+    CK(cudaMemcpyAsync(&par, fs->d_loop, sizeof(par), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *rounds = par.rounds;
+    h->last_shifts += (int64_t)par.shifts;
+    if (par.stopped) {
+        set_error("h2_kth_eig: bisection did not converge within 4096 rounds");
+        return H2_ERR_NUMERICAL;
+    }
+    return H2_OK;
+}
+
+int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out, double* err_bound,
+            const double* interval) {
     Workspace& ws = h->ws;
     FactorState* fs = state_of(h);
     cudaStream_t st = h->stream;
@@ -3386,13 +3512,29 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
     for (int64_t i = 0; i < nk; ++i) ks[i] = k[order[i]];
     k = ks.data();
     CK(cudaMemsetAsync(ws.d_err, 0, 8 * sizeof(int), st));
-    // start interval: Gershgorin padded by 1e-6 ||A||_inf; check nu(a) = 0, nu(b) = n in FP64
-    const double a = h->glo - 1e-6 * h->norm_inf, b = h->ghi + 1e-6 * h->norm_inf;
-    if (ws.lanes >= 2) {
+    // start interval: the caller's [a, b] with nu(a) < k <= nu(b) for every k
+    // (checked in FP64), else the Gershgorin interval padded by 1e-6 ||A||_inf
+    // with nu(a) = 0 and nu(b) = n (checked)
+    const double a = interval ? interval[0] : h->glo - 1e-6 * h->norm_inf;
+    const double b = interval ? interval[1] : h->ghi + 1e-6 * h->norm_inf;
+    int64_t nu_a = 0, nu_b = h->n;
+    if (ws.lanes >= 2 || interval) {
         double sh[2] = {a, b}, mp[2];
         int64_t cnt[2] = {0, 0};
-        if ((rc = host_batch(h, sh, 2, 0, cnt, mp))) return rc;
-        if (cnt[0] != 0 || cnt[1] != h->n) {
+        if (ws.lanes >= 2) {
+            if ((rc = host_batch(h, sh, 2, 0, cnt, mp))) return rc;
+        } else if ((rc = host_batch(h, sh, 1, 0, cnt, mp)) || (rc = host_batch(h, sh + 1, 1, 0, cnt + 1, mp + 1))) {
+            return rc;
+        }
+        if (interval) {
+            nu_a = cnt[0];
+            nu_b = cnt[1];
+            if (!(nu_a < k[0] && k[nk - 1] <= nu_b)) {
+                set_error("h2_kth_eig_in: the interval does not hold every requested eigenvalue (nu(lo) = " +
+                          std::to_string(nu_a) + ", nu(hi) = " + std::to_string(nu_b) + ")");
+                return H2_ERR_INTERVAL;
+            }
+        } else if (cnt[0] != 0 || cnt[1] != h->n) {
             set_error("h2_kth_eig: nu(a) != 0 or nu(b) != n on the Gershgorin interval");
             return H2_ERR_INTERVAL;
         }
@@ -3408,6 +3550,8 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
             return rc;
         fs->nk_cap = (int)nk;
     }
+    if (!fs->d_loop && (rc = dalloc(&fs->d_loop, 1))) return rc;
+    const bool loop = use_graphs(h);
     std::vector<double> lo(nk, a), hi(nk, b);
     CK(cudaMemcpyAsync(fs->d_lo, lo.data(), nk * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(fs->d_hi, hi.data(), nk * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -3418,13 +3562,20 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
     h->last_mixed_rounds = 0;
     if (h->opt.precision == H2_PREC_MIXED) {
         // mixed rounds while the brackets are wider than Delta = 64 u_32 ||A||_inf
-        const double delta = 64.0 * 0x1.0p-24 * h->norm_inf;
-        while (true) {
-            if ((rc = kth_round(h, (int)nk, std::max(tol, delta), 1, &nact))) return rc;
-            if (nact == 0) break;
-            ++rounds;
-            ++h->last_mixed_rounds;
-            if (rounds > 4096) { set_error("h2_kth_eig: no convergence"); return H2_ERR_NUMERICAL; }
+        const double delta = guard_delta(h);
+        if (loop) {
+            int r = 0;
+            if ((rc = run_loop(h, (int)nk, std::max(tol, delta), 1, &r))) return rc;
+            rounds += r;
+            h->last_mixed_rounds += r;
+        } else {
+            while (true) {
+                if ((rc = kth_round(h, (int)nk, std::max(tol, delta), 1, &nact))) return rc;
+                if (nact == 0) break;
+                ++rounds;
+                ++h->last_mixed_rounds;
+                if (rounds > 4096) { set_error("h2_kth_eig: no convergence"); return H2_ERR_NUMERICAL; }
+            }
         }
         // widen every bracket by Delta and verify it in FP64: nu(lo) < k <= nu(hi);
         // a bracket that fails restarts from the Gershgorin interval
@@ -3452,8 +3603,8 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
             return cnt[j];
         };
         for (int64_t i = 0; i < nk; ++i) {
-            int64_t cl = (lo[i] == a) ? 0 : count_at(lo[i]);
-            int64_t ch = (hi[i] == b) ? h->n : count_at(hi[i]);
+            int64_t cl = (lo[i] == a) ? nu_a : count_at(lo[i]);
+            int64_t ch = (hi[i] == b) ? nu_b : count_at(hi[i]);
             if (!(cl < k[i] && k[i] <= ch)) {
                 lo[i] = a;
                 hi[i] = b;
@@ -3464,11 +3615,17 @@ int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
         CK(cudaMemcpyAsync(fs->d_hi, hi.data(), nk * sizeof(double), cudaMemcpyHostToDevice, st));
     }
     // FP64 rounds to the requested width (Algorithm 1's stopping rule)
-    while (true) {
-        if ((rc = kth_round(h, (int)nk, tol, 0, &nact))) return rc;
-        if (nact == 0) break;
-        ++rounds;
-        if (rounds > 4096) { set_error("h2_kth_eig: bisection did not converge"); return H2_ERR_NUMERICAL; }
+    if (loop) {
+        int r = 0;
+        if ((rc = run_loop(h, (int)nk, tol, 0, &r))) return rc;
+        rounds += r;
+    } else {
+        while (true) {
+            if ((rc = kth_round(h, (int)nk, tol, 0, &nact))) return rc;
+            if (nact == 0) break;
+            ++rounds;
+            if (rounds > 4096) { set_error("h2_kth_eig: bisection did not converge"); return H2_ERR_NUMERICAL; }
+        }
     }
     h->last_rounds = rounds;
     CK(cudaMemcpyAsync(lo.data(), fs->d_lo, nk * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -3513,6 +3670,9 @@ void free_workspace(h2_matrix* h) {
         cudaFree(fs->d_lo); cudaFree(fs->d_hi); cudaFree(fs->d_k); cudaFree(fs->d_nact); cudaFree(fs->d_first);
         cudaFree(fs->d_req); cudaFree(fs->d_gc); cudaFree(fs->d_gmp); cudaFree(fs->d_rr_idx); cudaFree(fs->d_rr_n);
         cudaFree(fs->d_tally);
+        cudaFree(fs->d_loop);
+        for (auto& e : fs->loop_exec)
+            if (e) cudaGraphExecDestroy(e);
         delete fs;
     }
     ws.graph_state = nullptr;

@@ -160,7 +160,7 @@ int run_inertia_host(h2_matrix* h, const double* shifts, int64_t ns, int64_t* co
 int run_profile(h2_matrix* h, const double* d_shifts, int ns, int64_t* d_counts, double* ms,
                 int64_t* launches, double* flops, double* bytes);
 int run_kth(h2_matrix* h, const int64_t* k, int64_t nk, double tol, double* out,
-            double* err_bound);
+            double* err_bound, const double* interval);   // interval: nullable [lo, hi]
 void free_workspace(h2_matrix* h);
 int run_status(h2_matrix* h, int64_t* info);
 int tune_choice(h2_matrix* h, int level, int* out);
