@@ -859,6 +859,33 @@ def _serving(args):
     return res
 
 
+def _ncu_case(args):
+    """A small, fixed workload for ncu captures: one handle of the bench
+    configuration in the given precision with --lanes lanes, --warmup +
+    --steps device-resident batches, one line of output."""
+    import torch
+    import paper_2311_08618_gb300 as pkg
+    from paper_2311_08618_gb300 import build
+    build.build()
+    prec = {"fp64": pkg.H2_PREC_FP64, "mixed": pkg.H2_PREC_MIXED, "fp64_tc": pkg.H2_PREC_FP64_TC,
+            "fp64_tc_tcgen05": pkg.H2_PREC_FP64_TC}[args.ncu_case]
+    st = torch.cuda.Stream()
+    X = _points(WORKLOAD)
+    M = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
+                     eta=WORKLOAD["eta"], max_lanes=args.lanes, stream=st.cuda_stream, precision=prec,
+                     tc_schur=1 if args.ncu_case == "fp64_tc_tcgen05" else 0)
+    info = M.h2_info()
+    sh = torch.tensor(_shift_batches(info["gershgorin_lo"], info["gershgorin_hi"], args.lanes, 1)[0],
+                      dtype=torch.float64, device="cuda")
+    c = torch.zeros(args.lanes, dtype=torch.int64, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        M.h2_inertia_device(sh, args.lanes, c)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": args.ncu_case, "lanes": args.lanes, "batches": args.warmup + args.steps,
+                      "kernels_per_batch": info["kernels_per_batch"], "negative_counts_sum": int(c.sum())}))
+    M.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -888,6 +915,8 @@ def main():
     ap.add_argument("--serving-lanes", type=int, default=16)
     ap.add_argument("--workload", default="laplace2d_n1024", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1], help="0 FP64, 1 mixed (main handle)")
+    ap.add_argument("--ncu-case", default="", choices=["", "fp64", "mixed", "fp64_tc", "fp64_tc_tcgen05"],
+                    help="run only a small fixed workload for ncu captures")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -897,6 +926,8 @@ def main():
     try:
         if args.impl == "reference":
             reference_arm(args, rank, world, dist)
+        elif args.ncu_case:
+            _ncu_case(args)
         elif args.circle_sweep:
             _circle_sweep(args)
         else:

@@ -119,6 +119,13 @@ typedef struct {
                             max_lanes (max_lanes = 0: no other bound); h2_build
                             fails with H2_ERR_OOM when one lane does not fit.
                             h2_info reports the lanes and bytes chosen */
+    int tc_schur;        /* H2_PREC_FP64_TC, levels whose blocks have at most 64
+                            rows: 1 = the Schur digit products on the
+                            5th-generation tensor cores (tcgen05.mma, tensor-
+                            memory accumulators; one CTA per 128-row panel of an
+                            elimination's stacked targets), 0 (default) =
+                            warp-level mma.sync tiles of 32 x 32.  Both give the
+                            same values */
 } h2_options;
 
 /* Fills *opt with the defaults above.  Never fails. */

@@ -1465,6 +1465,8 @@ struct SchurArgs {
     ScratchLayout lay;
     const int* active;
     int* err;
+    const int* ntarg;   // targets of each elimination of the colour (tcgen05 kernel)
+    int npanel;         // 128-row panels per elimination (tcgen05 kernel)
 };
 
 // S_ab[i0:i0+32, j0:j0+32] -= W_a Y_b^T (Eq. blr2-diag-schur).  T is the
@@ -1712,6 +1714,263 @@ __global__ void __launch_bounds__(NT, 3) k_schur_oz(SchurArgs A) { k_schur_oz_bo
 __global__ void __launch_bounds__(NT, 3) k_schur_oz_g(GroupArgs<SchurArgs> G) {
     const int m = group_find(G.off, G.n, blockIdx.x);
     k_schur_oz_body(G.args[m], blockIdx.x - G.off[m], blockIdx.y);
+}
+
+// ---- The same digit products on the 5th-generation tensor cores (tcgen05).
+// Per (elimination, lane) the Schur updates of all target pairs form one
+// block-lower-triangular product: the rows of W of every target stacked
+// (target order, live rows only) against the rows of Y stacked the same way.
+// One CTA takes a panel of 128 stacked rows of W: their 8 digit planes stay
+// in shared memory (the MMA's A operand, M = 128), and the stacked rows of Y
+// stream through in chunks of 32 (B operand, N = 32), double-buffered.  For
+// every chunk one thread issues the 36 digit-pair products (K in steps of 16)
+// into 8 FP32 level accumulators in tensor memory (level s = p + q, 8 x 32
+// columns), so that the chunk's products run on the tensor core while the
+// CTA's threads fold the previous chunk: each thread owns one row (one TMEM
+// lane), reads its 8 levels, folds them into the exact int64 pair (hi, lo) of
+// k_schur_oz and rounds once (oz_value).  With K <= 64 every level sum is an
+// integer of magnitude < 8 * 64 * 127^2 < 2^23, exact in FP32.  The values,
+// the element convention of diagonal pairs (32 x 32 tiles on the tile
+// diagonal written whole, lower tiles also mirrored, upper tiles skipped) and
+// hence the results are those of k_schur_oz.
+// Operands sit in shared memory in the no-swizzle K-major layout of 8-row x
+// 16-byte core matrices: element (r, k) of a plane at (r / 8) * 1024 +
+// (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2 bytes (K-direction core stride
+// 128 B, 8-row stride 1024 B).
+constexpr int TCM = 128;                        // panel rows (MMA M)
+constexpr int TCN = 32;                         // chunk rows of Y (MMA N)
+constexpr int TCK = 64;                         // largest K held (digit columns)
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_APLANE = TCM * TCK * 2;   // bytes of one digit plane of the panel
+constexpr uint32_t TC_BPLANE = TCN * TCK * 2;   // bytes of one digit plane of a chunk
+constexpr size_t TC_SMEM = (size_t)OZP * TC_APLANE + 2 * (size_t)OZP * TC_BPLANE;
+constexpr long TC_WAIT_LIMIT = 1L << 26;        // polls of an mbarrier before giving up
+
+__device__ __forceinline__ uint32_t tc_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, K-direction core stride
+// (128 B), 8-row stride (1024 B), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t idesc, int accum) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+                 "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (long it = 0; it < TC_WAIT_LIMIT && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(tc_saddr(bar)), "r"(parity) : "memory");
+    return done != 0;
+}
+
+// 8 consecutive TMEM columns of this warp's 32 lanes
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void k_schur_tc_body(const SchurArgs& A, const int bx, const int by) {
+    HbScope hb_(5);
+    const int lane = by;
+    if (lane >= *A.active) return;
+    const int ci = bx / A.npanel, panel = bx % A.npanel;
+    const int D = A.D, dk = A.lay.dk;
+    const double* scr = A.scratch + ((size_t)ci * A.lanes + lane) * A.lay.total;
+    const int* hdr = (const int*)(scr + A.lay.hdr);
+    const int Rp = hdr[1];
+    const int nt = A.ntarg[ci];
+    if (Rp <= 0 || nt <= 0) return;
+    if (Rp > TCK || Rp > D || dk > TCK || nt > 64) {
+        if (threadIdx.x == 0 && panel == 0) report_bad(A.err, 7, Rp, D, dk, nt);
+        return;
+    }
+    // stacked live rows of the targets (prefix sums), the same for every thread
+    __shared__ int pre[65];
+    __shared__ int rowt[TCM], rowi[TCM];      // panel row -> (target, row)
+    __shared__ int colt[2][TCN], colj[2][TCN];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_poff;
+    if (threadIdx.x == 0) {
+        int acc = 0, bad = 0;
+        pre[0] = 0;
+        for (int t = 0; t < nt; ++t) {
+            const int r = hdr[HDR_ROWS + t];
+            bad |= (r < 0 || r > D);
+            acc += max(0, min(r, D));
+            pre[t + 1] = acc;
+        }
+        if (bad) report_bad(A.err, 7, Rp, D, nt, -1);
+        int po = 0;                            // first pair of this elimination
+        for (int c = 0; c < ci; ++c) po += A.ntarg[c] * (A.ntarg[c] + 1) / 2;
+        s_poff = po;
+    }
+    __syncthreads();
+    const int total = pre[nt];
+    const int g0 = panel * TCM;
+    if (g0 >= total) return;                   // uniform: nothing staged, nothing allocated
+    const int R = threadIdx.x;                 // this thread's panel row = TMEM lane
+    {
+        const int g = g0 + R;
+        int t = -1, i = 0;
+        if (g < total) {
+            t = 0;
+            while (pre[t + 1] <= g) ++t;
+            i = g - pre[t];
+        }
+        rowt[R] = t;
+        rowi[R] = i;
+    }
+    __syncthreads();
+    const int tmax = rowt[min(TCM, total - g0) - 1];
+    const int colmax = pre[tmax + 1];          // pairs (t, u) need u <= t
+    const int nchunk = (colmax + TCN - 1) / TCN;
+    const int nks = (Rp + 15) / 16;            // K steps of 16 (zero digits up to 32-aligned Rp)
+    const int nkc = 2 * nks;                   // 16-byte chunks of a staged row
+    extern __shared__ __align__(128) uint8_t tcsm[];
+    uint8_t* sA = tcsm;
+    uint8_t* sB = tcsm + (size_t)OZP * TC_APLANE;
+    const uint16_t* wd = reinterpret_cast<const uint16_t*>(scr + A.lay.wd);
+    const uint16_t* yd = reinterpret_cast<const uint16_t*>(scr + A.lay.yd);
+    const int* we = reinterpret_cast<const int*>(scr + A.lay.we);
+    const int* ye = reinterpret_cast<const int*>(scr + A.lay.ye);
+    // A: the panel's 8 digit planes (rows past the stack are zero)
+    for (int e = threadIdx.x; e < OZP * TCM * nkc; e += TC_THREADS) {
+        const int p = e / (TCM * nkc), rem = e % (TCM * nkc), r = rem / nkc, c = rem % nkc;
+        int4 v = make_int4(0, 0, 0, 0);
+        const int t = rowt[r];
+        if (t >= 0)
+            v = *reinterpret_cast<const int4*>(&wd[(((size_t)t * OZP + p) * D + rowi[r]) * dk + 8 * c]);
+        *reinterpret_cast<int4*>(sA + (size_t)p * TC_APLANE + (r / 8) * 1024 + c * 128 + (r % 8) * 16) = v;
+    }
+    const int w = threadIdx.x / 32;
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_saddr(&tmem_base)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_saddr(&bar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_saddr(&bar[1])), "r"(1));
+    }
+    // B chunk c of the stacked Y rows into buffer c % 2, with its column map
+    auto stage_b = [&](int c) {
+        const int b = c & 1;
+        __syncthreads();             // every thread is done with chunk c - 2's columns and maps
+        if (threadIdx.x < TCN) {
+            const int g = c * TCN + threadIdx.x;
+            int u = -1, j = 0;
+            if (g < colmax) {
+                u = 0;
+                while (pre[u + 1] <= g) ++u;
+                j = g - pre[u];
+            }
+            colt[b][threadIdx.x] = u;
+            colj[b][threadIdx.x] = j;
+        }
+        __syncthreads();
+        uint8_t* dst = sB + (size_t)b * OZP * TC_BPLANE;
+        for (int e = threadIdx.x; e < OZP * TCN * nkc; e += TC_THREADS) {
+            const int q = e / (TCN * nkc), rem = e % (TCN * nkc), r = rem / nkc, cc = rem % nkc;
+            int4 v = make_int4(0, 0, 0, 0);
+            const int u = colt[b][r];
+            if (u >= 0)
+                v = *reinterpret_cast<const int4*>(&yd[(((size_t)u * OZP + q) * D + colj[b][r]) * dk + 8 * cc]);
+            *reinterpret_cast<int4*>(dst + (size_t)q * TC_BPLANE + (r / 8) * 1024 + cc * 128 + (r % 8) * 16) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    };
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCN >> 3) << 17) | ((uint32_t)(TCM >> 4) << 24);
+    auto issue = [&](int c) {
+        if (threadIdx.x != 0) return;
+        const int b = c & 1;
+        const uint32_t dcol = tmem_base + (uint32_t)(b * OZP * TCN);
+        const uint32_t a0 = tc_saddr(sA), b0 = tc_saddr(sB + (size_t)b * OZP * TC_BPLANE);
+        for (int lv = 0; lv < OZP; ++lv)
+            for (int p = 0; p <= lv; ++p)
+                for (int ks = 0; ks < nks; ++ks)
+                    tc_mma(dcol + (uint32_t)(lv * TCN), tc_desc(a0 + p * TC_APLANE + ks * 256),
+                           tc_desc(b0 + (lv - p) * TC_BPLANE + ks * 256), idesc, (p | ks) != 0);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         tc_saddr(&bar[b]))
+                     : "memory");
+    };
+    // this thread's row: target, row, exponent
+    const int myt = rowt[R], myi = rowi[R];
+    const int myexp = myt >= 0 ? we[myt * D + myi] : 0;
+    double* const slots = A.slots;
+    const SchurPair* pairs = A.pairs + s_poff;
+    bool ok = true;
+    stage_b(0);
+    issue(0);
+    for (int c = 0; c < nchunk && ok; ++c) {
+        const int b = c & 1;
+        if (c + 1 < nchunk) {
+            stage_b(c + 1);          // buffer (c+1)%2 and its TMEM columns are free: chunk c-1 is folded
+            issue(c + 1);
+        }
+        // every thread agrees on the outcome of its bounded wait
+        if (!__syncthreads_and(tc_wait(&bar[b], (uint32_t)((c >> 1) & 1)) ? 1 : 0)) {
+            ok = false;
+            if (threadIdx.x == 0) report_bad(A.err, 7, c, nchunk, -2, -2);
+            // let the chunks in flight finish (bounded) before their columns are freed
+            tc_wait(&bar[b], (uint32_t)((c >> 1) & 1));
+            if (c + 1 < nchunk) tc_wait(&bar[(c + 1) & 1], (uint32_t)(((c + 1) >> 1) & 1));
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t trow = tmem_base + ((uint32_t)(32 * w) << 16) + (uint32_t)(b * OZP * TCN);
+        for (int j0 = 0; j0 < TCN; j0 += 8) {
+            float lvv[OZP][8];
+#pragma unroll
+            for (int lv = 0; lv < OZP; ++lv) tc_ld8(trow + (uint32_t)(lv * TCN + j0), lvv[lv]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (myt < 0) continue;
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const int u = colt[b][j0 + jj];
+                if (u < 0 || u > myt) continue;
+                const int j = colj[b][j0 + jj];
+                const bool diag = u == myt;
+                const int ti = myi / TS, tj = j / TS;
+                if (diag && ti < tj) continue;
+                long long h = __float2ll_rn(lvv[0][jj]);
+                h = h * 128 + __float2ll_rn(lvv[1][jj]);
+                h = h * 128 + __float2ll_rn(lvv[2][jj]);
+                h = h * 128 + __float2ll_rn(lvv[3][jj]);
+                long long g = __float2ll_rn(lvv[4][jj]);
+                g = g * 128 + __float2ll_rn(lvv[5][jj]);
+                g = g * 128 + __float2ll_rn(lvv[6][jj]);
+                g = g * 128 + __float2ll_rn(lvv[7][jj]);
+                const double v = oz_value(h, g, myexp, ye[u * D + j]);
+                const SchurPair P = pairs[myt * (myt + 1) / 2 + u];
+                double* Bk = slot_ptr(slots, P.slot, A.lanes, lane, D);
+                belem(Bk, D, P.trans, myi, j) -= v;
+                if (diag && ti > tj) belem(Bk, D, P.trans, j, myi) -= v;
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512));
+}
+__global__ void __launch_bounds__(TC_THREADS, 1) k_schur_tc(SchurArgs A) { k_schur_tc_body(A, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(TC_THREADS, 1) k_schur_tc_g(GroupArgs<SchurArgs> G) {
+    const int m = group_find(G.off, G.n, blockIdx.x);
+    k_schur_tc_body(G.args[m], blockIdx.x - G.off[m], blockIdx.y);
 }
 
 // Mixed path: S_ab[i0:i0+64, j0:j0+64] -= W_a Y_b^T (Eq. blr2-diag-schur) with
@@ -2361,6 +2620,7 @@ int alloc_workspace(h2_matrix* h, int lanes) {
     CK(cudaFuncSetAttribute(k_ldl_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     CK(cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
     CK(cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     // buffers
     ws.d_slots.assign(L + 1, nullptr);
     ws.d_dim.assign(L + 1, nullptr);
@@ -2573,13 +2833,22 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
             {
                 const int ts = mixed ? TSF : TS;
                 const int tdim = (D.dmax + ts - 1) / ts;
+                const int npanel = (C.ntarg_max * D.dmax + TCM - 1) / TCM;
                 LaunchRec q = r;
                 q.op = OP_SCHUR;
                 q.kind = H2_KIND_SCHUR;
                 q.sa = SchurArgs{ws.d_slots[l], D.dmax, LN, C.pairs, tdim * tdim, tdim, ws.d_scratch, W.lay,
-                                 fs->d_active, ws.d_err};
+                                 fs->d_active, ws.d_err, C.ntarg, npanel};
                 q.variant = mixed ? 1 : (h->opt.precision == H2_PREC_FP64_TC ? 2 : 0);
                 q.grid = dim3(C.npairs * tdim * tdim, LN);
+                // FP64_TC with blocks of at most 64 rows: the tcgen05 kernel (one
+                // CTA per 128-row panel of an elimination's stacked targets)
+                if (q.variant == 2 && h->opt.tc_schur != 0 && D.dmax <= TCK && W.lay.dk <= TCK) {
+                    q.variant = 3;
+                    q.block = TC_THREADS;
+                    q.smem = TC_SMEM;
+                    q.grid = dim3(C.ncl * npanel, LN);
+                }
                 R.push_back(q);
             }
         }
@@ -2653,6 +2922,7 @@ static void launch_single(const LaunchRec& r, cudaStream_t st) {
         case OP_SCHUR:
             if (r.variant == 1) k_schur_f32<<<r.grid, NT, 0, st>>>(r.sa);
             else if (r.variant == 2) k_schur_oz<<<r.grid, NT, 0, st>>>(r.sa);
+            else if (r.variant == 3) k_schur_tc<<<r.grid, TC_THREADS, r.smem, st>>>(r.sa);
             else k_schur<double><<<r.grid, NT, 0, st>>>(r.sa);
             break;
         case OP_MERGE: k_merge<<<r.grid, NT, 0, st>>>(r.ma); break;
@@ -2835,6 +3105,7 @@ static void launch_grouped(const GLaunch& gl, cudaStream_t st) {
         case OP_SCHUR:
             if (gl.variant == 1) k_schur_f32_g<<<grid, NT, 0, st>>>(S);
             else if (gl.variant == 2) k_schur_oz_g<<<grid, NT, 0, st>>>(S);
+            else if (gl.variant == 3) k_schur_tc_g<<<grid, TC_THREADS, gl.smem, st>>>(S);
             else k_schur_g<double><<<grid, NT, 0, st>>>(S);
             break;
         case OP_MERGE:
@@ -2933,6 +3204,7 @@ int group_create(h2_matrix* const* hs, int nh, h2_group_set** out) {
     CK(cudaFuncSetAttribute(k_ldl_g<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
     CK(cudaFuncSetAttribute(k_trsm_g<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
     CK(cudaFuncSetAttribute(k_trsm_g<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap + 8192));
+    CK(cudaFuncSetAttribute(k_schur_tc_g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     int rc = group_graph(g, g->mixed, g->recs, g->launches, &g->graph);
     if (rc == H2_OK && g->mixed) rc = group_graph(g, 0, g->recs64, g->launches64, &g->graph64);
     if (rc) {

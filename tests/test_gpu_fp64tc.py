@@ -114,3 +114,30 @@ def test_fp64tc_wide_redundant_blocks(pkg):
     assert sure.sum() >= len(s) // 2
     want = np.array([np.sum(ev < x) for x in s])
     assert np.array_equal(ct[sure], want[sure])
+
+
+@pytest.mark.parametrize("n,d,leaf,rank,lanes", [(1024, 2, 64, 16, 256), (600, 3, 40, 16, 16), (2048, 2, 32, 12, 64)])
+def test_tcgen05_schur_bit_identical_to_mma_sync(pkg, n, d, leaf, rank, lanes):
+    """The tcgen05 digit Schur kernel (tensor-memory accumulators, 128-row
+    panels) and the mma.sync one form the same exact integer level sums and
+    round once the same way: counts and min |pivot| agree bit for bit."""
+    import torch
+    X = W.uniform_cube(n, d, 91)
+    kp = (1e-3, 0, 0, 0)
+    mats = [pkg.H2Matrix(X, W.LAPLACE_EPS, kp, leaf=leaf, rank=rank, max_lanes=lanes,
+                         precision=pkg.H2_PREC_FP64_TC, tc_schur=t) for t in (1, 0)]
+    info = mats[0].h2_info()
+    sh = torch.tensor(info["gershgorin_lo"] + (info["gershgorin_hi"] - info["gershgorin_lo"]) *
+                      (np.arange(lanes) + 0.37) / lanes, dtype=torch.float64, device="cuda")
+    out = []
+    for M in mats:
+        c = torch.zeros(lanes, dtype=torch.int64, device="cuda")
+        mp = torch.zeros(lanes, dtype=torch.float64, device="cuda")
+        M.h2_inertia_device(sh, lanes, c, mp)
+        torch.cuda.synchronize()
+        assert M.h2_status()[0] == 0
+        out.append((c.cpu().numpy(), mp.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1].view(np.int64), out[1][1].view(np.int64))
+    for M in mats:
+        M.close()
