@@ -67,8 +67,8 @@ FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 (profiling recipe table); not i
 # profiles/k_schur_laplace2d_n1024_256lanes.md; valid for that workload and lane
 # count while the kernel's source is unchanged (sha256 prefix of its text)
 NCU_TRAFFIC = {"kernel": "k_schur", "workload": "laplace2d_n1024", "lanes": 256,
-               "bytes_per_launch": 323.52e6, "source_sha": "840ceb67eabf6157"}
-KERNEL_REGIONS = {"k_schur": ("h2_factor.cu", "struct SchurArgs {",
+               "bytes_per_launch": 323.52e6, "source_sha": "7ddfe31f5f9903ac"}
+KERNEL_REGIONS = {"k_schur": ("h2_factor.cu", "// S_ab[i0:i0+32, j0:j0+32] -= W_a Y_b^T (Eq. blr2-diag-schur).",
                                "// FP64-accurate Schur products on the tensor cores")}
 
 
