@@ -1722,17 +1722,19 @@ __global__ void __launch_bounds__(NT, 3) k_schur_oz_g(GroupArgs<SchurArgs> G) {
 // (target order, live rows only) against the rows of Y stacked the same way.
 // One CTA takes a panel of 128 stacked rows of W: their 8 digit planes stay
 // in shared memory (the MMA's A operand, M = 128), and the stacked rows of Y
-// stream through in chunks of 32 (B operand, N = 32), double-buffered.  For
-// every chunk one thread issues the 36 digit-pair products (K in steps of 16)
-// into 8 FP32 level accumulators in tensor memory (level s = p + q, 8 x 32
-// columns), so that the chunk's products run on the tensor core while the
-// CTA's threads fold the previous chunk: each thread owns one row (one TMEM
-// lane), reads its 8 levels, folds them into the exact int64 pair (hi, lo) of
-// k_schur_oz and rounds once (oz_value).  With K <= 64 every level sum is an
-// integer of magnitude < 8 * 64 * 127^2 < 2^23, exact in FP32.  The values,
-// the element convention of diagonal pairs (32 x 32 tiles on the tile
-// diagonal written whole, lower tiles also mirrored, upper tiles skipped) and
-// hence the results are those of k_schur_oz.
+// stream through in chunks of 32 (B operand, N = 32).  For every chunk one
+// thread issues the 36 digit-pair products (K in steps of 16) into 8 FP32
+// level accumulators in tensor memory (level s = p + q, 8 x 32 columns, two
+// buffers).  A three-stage pipeline keeps the units busy: while the threads
+// fold chunk c, the tensor core multiplies chunk c + 1 and cp.async brings
+// chunk c + 2 into shared memory.  Warp w reads the tensor-memory lanes of its
+// quarter (w mod 4: 32 panel rows) and folds 8 of the 32 columns (w / 4):
+// every thread folds its row's 8 level sums of a column into the exact int64
+// pair (hi, lo) of k_schur_oz and rounds once (oz_value).  With K <= 64 every
+// level sum is an integer of magnitude < 8 * 64 * 127^2 < 2^23, exact in
+// FP32.  The values, the element convention of diagonal pairs (32 x 32 tiles
+// on the tile diagonal written whole, lower tiles also mirrored, upper tiles
+// skipped) and hence the results are those of k_schur_oz.
 // Operands sit in shared memory in the no-swizzle K-major layout of 8-row x
 // 16-byte core matrices: element (r, k) of a plane at (r / 8) * 1024 +
 // (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2 bytes (K-direction core stride
@@ -1740,7 +1742,7 @@ __global__ void __launch_bounds__(NT, 3) k_schur_oz_g(GroupArgs<SchurArgs> G) {
 constexpr int TCM = 128;                        // panel rows (MMA M)
 constexpr int TCN = 32;                         // chunk rows of Y (MMA N)
 constexpr int TCK = 64;                         // largest K held (digit columns)
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 512;                 // 16 warps: 4 per tensor-memory quarter
 constexpr uint32_t TC_APLANE = TCM * TCK * 2;   // bytes of one digit plane of the panel
 constexpr uint32_t TC_BPLANE = TCN * TCK * 2;   // bytes of one digit plane of a chunk
 constexpr size_t TC_SMEM = (size_t)OZP * TC_APLANE + 2 * (size_t)OZP * TC_BPLANE;
@@ -1769,6 +1771,16 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
     return done != 0;
 }
 
+// 16 bytes global -> shared without passing through registers; src_bytes = 0
+// writes zeros (nothing is read)
+__device__ __forceinline__ void tc_cp16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc_saddr(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void tc_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // 8 consecutive TMEM columns of this warp's 32 lanes
 __device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
     uint32_t r[8];
@@ -1777,6 +1789,13 @@ __device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
                  : "r"(taddr));
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// the stacked row g < pre[nt] as (target, row): targets are few, a linear scan
+__device__ __forceinline__ int tc_target_of(const int* pre, int g) {
+    int t = 0;
+    while (pre[t + 1] <= g) ++t;
+    return t;
 }
 
 __device__ __forceinline__ void k_schur_tc_body(const SchurArgs& A, const int bx, const int by) {
@@ -1797,7 +1816,6 @@ __device__ __forceinline__ void k_schur_tc_body(const SchurArgs& A, const int bx
     // stacked live rows of the targets (prefix sums), the same for every thread
     __shared__ int pre[65];
     __shared__ int rowt[TCM], rowi[TCM];      // panel row -> (target, row)
-    __shared__ int colt[2][TCN], colj[2][TCN];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_poff;
@@ -1819,17 +1837,15 @@ __device__ __forceinline__ void k_schur_tc_body(const SchurArgs& A, const int bx
     const int total = pre[nt];
     const int g0 = panel * TCM;
     if (g0 >= total) return;                   // uniform: nothing staged, nothing allocated
-    const int R = threadIdx.x;                 // this thread's panel row = TMEM lane
-    {
-        const int g = g0 + R;
+    if (threadIdx.x < TCM) {
+        const int g = g0 + threadIdx.x;
         int t = -1, i = 0;
         if (g < total) {
-            t = 0;
-            while (pre[t + 1] <= g) ++t;
+            t = tc_target_of(pre, g);
             i = g - pre[t];
         }
-        rowt[R] = t;
-        rowi[R] = i;
+        rowt[threadIdx.x] = t;
+        rowi[threadIdx.x] = i;
     }
     __syncthreads();
     const int tmax = rowt[min(TCM, total - g0) - 1];
@@ -1847,12 +1863,11 @@ __device__ __forceinline__ void k_schur_tc_body(const SchurArgs& A, const int bx
     // A: the panel's 8 digit planes (rows past the stack are zero)
     for (int e = threadIdx.x; e < OZP * TCM * nkc; e += TC_THREADS) {
         const int p = e / (TCM * nkc), rem = e % (TCM * nkc), r = rem / nkc, c = rem % nkc;
-        int4 v = make_int4(0, 0, 0, 0);
         const int t = rowt[r];
-        if (t >= 0)
-            v = *reinterpret_cast<const int4*>(&wd[(((size_t)t * OZP + p) * D + rowi[r]) * dk + 8 * c]);
-        *reinterpret_cast<int4*>(sA + (size_t)p * TC_APLANE + (r / 8) * 1024 + c * 128 + (r % 8) * 16) = v;
+        const uint16_t* src = t >= 0 ? &wd[(((size_t)t * OZP + p) * D + rowi[r]) * dk + 8 * c] : wd;
+        tc_cp16(sA + (size_t)p * TC_APLANE + (r / 8) * 1024 + c * 128 + (r % 8) * 16, src, t >= 0 ? 16 : 0);
     }
+    tc_cp_commit();
     const int w = threadIdx.x / 32;
     if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_saddr(&tmem_base)),
@@ -1863,37 +1878,25 @@ __device__ __forceinline__ void k_schur_tc_body(const SchurArgs& A, const int bx
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_saddr(&bar[0])), "r"(1));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_saddr(&bar[1])), "r"(1));
     }
-    // B chunk c of the stacked Y rows into buffer c % 2, with its column map
-    auto stage_b = [&](int c) {
-        const int b = c & 1;
-        __syncthreads();             // every thread is done with chunk c - 2's columns and maps
-        if (threadIdx.x < TCN) {
-            const int g = c * TCN + threadIdx.x;
-            int u = -1, j = 0;
-            if (g < colmax) {
-                u = 0;
-                while (pre[u + 1] <= g) ++u;
-                j = g - pre[u];
-            }
-            colt[b][threadIdx.x] = u;
-            colj[b][threadIdx.x] = j;
-        }
-        __syncthreads();
-        uint8_t* dst = sB + (size_t)b * OZP * TC_BPLANE;
+    // cp.async of chunk c's 8 digit planes (stacked Y rows 32c ..) into buffer c % 2
+    auto chunk_load = [&](int c) {
+        uint8_t* dst = sB + (size_t)(c & 1) * OZP * TC_BPLANE;
         for (int e = threadIdx.x; e < OZP * TCN * nkc; e += TC_THREADS) {
             const int q = e / (TCN * nkc), rem = e % (TCN * nkc), r = rem / nkc, cc = rem % nkc;
-            int4 v = make_int4(0, 0, 0, 0);
-            const int u = colt[b][r];
-            if (u >= 0)
-                v = *reinterpret_cast<const int4*>(&yd[(((size_t)u * OZP + q) * D + colj[b][r]) * dk + 8 * cc]);
-            *reinterpret_cast<int4*>(dst + (size_t)q * TC_BPLANE + (r / 8) * 1024 + cc * 128 + (r % 8) * 16) = v;
+            const int g = c * TCN + r;
+            const uint16_t* src = yd;
+            int nb = 0;
+            if (g < colmax) {
+                const int u = tc_target_of(pre, g);
+                src = &yd[(((size_t)u * OZP + q) * D + (g - pre[u])) * dk + 8 * cc];
+                nb = 16;
+            }
+            tc_cp16(dst + (size_t)q * TC_BPLANE + (r / 8) * 1024 + cc * 128 + (r % 8) * 16, src, nb);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tc_cp_commit();
     };
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCN >> 3) << 17) | ((uint32_t)(TCM >> 4) << 24);
+    // thread 0: the 36 x nks products of chunk c into tensor-memory buffer c % 2
     auto issue = [&](int c) {
         if (threadIdx.x != 0) return;
         const int b = c & 1;
@@ -1908,62 +1911,108 @@ __device__ __forceinline__ void k_schur_tc_body(const SchurArgs& A, const int bx
                          tc_saddr(&bar[b]))
                      : "memory");
     };
-    // this thread's row: target, row, exponent
+    // copies landed -> visible to the tensor core and to every thread; every
+    // thread is done reading the tensor-memory buffer the next products reuse
+    auto publish = [&]() {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    };
+    // this thread's row (tensor-memory lane) and its 8 columns of every chunk
+    const int quarter = w & 3, cgrp = w >> 2;
+    const int R = 32 * quarter + (threadIdx.x & 31);
     const int myt = rowt[R], myi = rowi[R];
     const int myexp = myt >= 0 ? we[myt * D + myi] : 0;
-    double* const slots = A.slots;
-    const SchurPair* pairs = A.pairs + s_poff;
-    bool ok = true;
-    stage_b(0);
+    // prologue: A and chunk 0 landed, chunk 1 in flight, products of chunk 0
+    chunk_load(0);
+    if (nchunk > 1) {
+        chunk_load(1);
+        tc_cp_wait<1>();
+    } else {
+        tc_cp_wait<0>();
+    }
+    publish();
     issue(0);
-    for (int c = 0; c < nchunk && ok; ++c) {
+    // Each thread waits for a chunk's products itself (bounded).  A wait that
+    // runs out is reported and the loop goes on, so that every thread meets
+    // the same barriers; the results of that call are then invalid.
+    int timed_out = 0;
+    for (int c = 0; c < nchunk; ++c) {
         const int b = c & 1;
-        if (c + 1 < nchunk) {
-            stage_b(c + 1);          // buffer (c+1)%2 and its TMEM columns are free: chunk c-1 is folded
-            issue(c + 1);
-        }
-        // every thread agrees on the outcome of its bounded wait
-        if (!__syncthreads_and(tc_wait(&bar[b], (uint32_t)((c >> 1) & 1)) ? 1 : 0)) {
-            ok = false;
-            if (threadIdx.x == 0) report_bad(A.err, 7, c, nchunk, -2, -2);
-            // let the chunks in flight finish (bounded) before their columns are freed
-            tc_wait(&bar[b], (uint32_t)((c >> 1) & 1));
-            if (c + 1 < nchunk) tc_wait(&bar[(c + 1) & 1], (uint32_t)(((c + 1) >> 1) & 1));
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t trow = tmem_base + ((uint32_t)(32 * w) << 16) + (uint32_t)(b * OZP * TCN);
-        for (int j0 = 0; j0 < TCN; j0 += 8) {
-            float lvv[OZP][8];
-#pragma unroll
-            for (int lv = 0; lv < OZP; ++lv) tc_ld8(trow + (uint32_t)(lv * TCN + j0), lvv[lv]);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (myt < 0) continue;
+        // this thread's 8 elements of chunk c: where they go, and S read early
+        // (the loads overlap the wait for the products and the fold)
+        const int gc = c * TCN + 8 * cgrp;         // this thread's first stacked column
+        double* dst[8];
+        double* mir[8];
+        double s0[8];
+        int ecol[8];
+        {
+            int u = gc < colmax ? tc_target_of(pre, gc) : nt;
+            int j = gc < colmax ? gc - pre[u] : 0;
+            double* Bk = nullptr;
+            int trans = 0, ucur = -1;
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
-                const int u = colt[b][j0 + jj];
-                if (u < 0 || u > myt) continue;
-                const int j = colj[b][j0 + jj];
-                const bool diag = u == myt;
-                const int ti = myi / TS, tj = j / TS;
-                if (diag && ti < tj) continue;
-                long long h = __float2ll_rn(lvv[0][jj]);
-                h = h * 128 + __float2ll_rn(lvv[1][jj]);
-                h = h * 128 + __float2ll_rn(lvv[2][jj]);
-                h = h * 128 + __float2ll_rn(lvv[3][jj]);
-                long long g = __float2ll_rn(lvv[4][jj]);
-                g = g * 128 + __float2ll_rn(lvv[5][jj]);
-                g = g * 128 + __float2ll_rn(lvv[6][jj]);
-                g = g * 128 + __float2ll_rn(lvv[7][jj]);
-                const double v = oz_value(h, g, myexp, ye[u * D + j]);
-                const SchurPair P = pairs[myt * (myt + 1) / 2 + u];
-                double* Bk = slot_ptr(slots, P.slot, A.lanes, lane, D);
-                belem(Bk, D, P.trans, myi, j) -= v;
-                if (diag && ti > tj) belem(Bk, D, P.trans, j, myi) -= v;
+                dst[jj] = nullptr;
+                mir[jj] = nullptr;
+                ecol[jj] = 0;
+                const bool col_ok = gc + jj < colmax;
+                if (col_ok && myt >= 0 && u <= myt && !(u == myt && myi / TS < j / TS)) {
+                    if (u != ucur) {
+                        const SchurPair P = A.pairs[s_poff + myt * (myt + 1) / 2 + u];
+                        Bk = slot_ptr(A.slots, P.slot, A.lanes, lane, D);
+                        trans = P.trans;
+                        ucur = u;
+                    }
+                    dst[jj] = &belem(Bk, D, trans, myi, j);
+                    if (u == myt && myi / TS > j / TS) mir[jj] = &belem(Bk, D, trans, j, myi);
+                    ecol[jj] = ye[u * D + j];
+                }
+                if (col_ok && ++j == pre[u + 1] - pre[u]) {      // next stacked column
+                    j = 0;
+                    ++u;
+                    while (u < nt - 1 && pre[u + 1] == pre[u]) ++u;
+                }
             }
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) s0[jj] = dst[jj] ? *dst[jj] : 0.0;
+        }
+        if (!tc_wait(&bar[b], (uint32_t)((c >> 1) & 1))) timed_out = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // chunk c + 2 into the buffer chunk c's products have released
+        if (c + 2 < nchunk) chunk_load(c + 2);
+        // chunk c + 1 landed: its products run while chunk c is folded
+        if (c + 1 < nchunk) {
+            if (c + 2 < nchunk) tc_cp_wait<1>();
+            else tc_cp_wait<0>();
+            publish();
+            issue(c + 1);
+        }
+        const uint32_t taddr = tmem_base + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * OZP * TCN + 8 * cgrp);
+        float lvv[OZP][8];
+#pragma unroll
+        for (int lv = 0; lv < OZP; ++lv) tc_ld8(taddr + (uint32_t)(lv * TCN), lvv[lv]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            if (!dst[jj]) continue;
+            long long h = __float2int_rn(lvv[0][jj]);
+            h = h * 128 + __float2int_rn(lvv[1][jj]);
+            h = h * 128 + __float2int_rn(lvv[2][jj]);
+            h = h * 128 + __float2int_rn(lvv[3][jj]);
+            long long g = __float2int_rn(lvv[4][jj]);
+            g = g * 128 + __float2int_rn(lvv[5][jj]);
+            g = g * 128 + __float2int_rn(lvv[6][jj]);
+            g = g * 128 + __float2int_rn(lvv[7][jj]);
+            const double v = oz_value(h, g, myexp, ecol[jj]);
+            *dst[jj] = s0[jj] - v;
+            if (mir[jj]) *mir[jj] -= v;
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
+    if (timed_out) report_bad(A.err, 7, nchunk, -2, -2, -2);
+    tc_cp_wait<0>();
     __syncthreads();
     if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512));
 }

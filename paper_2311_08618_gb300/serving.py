@@ -135,6 +135,8 @@ class Server:
         self.stream = torch.cuda.Stream()       # one stream for all resident matrices
         self.group = None                       # group batch over all resident matrices
         self._group_dirty = True
+        self.host_s = 0.0                       # time spent planning and narrowing on the host
+        self.wait_s = 0.0                       # time spent waiting for the device's batches
 
     # -- residency ----------------------------------------------------------
     def add_matrix(self, name, points, kernel, kparams, leaf, rank, eta=1.0, lanes=16, **opts):
@@ -240,6 +242,7 @@ class Server:
     # -- one tick ---------------------------------------------------------------
     def step(self):
         """Admit, run one multisection round on every busy matrix, update."""
+        t_host = time.perf_counter()
         self._admit()
         plans = {}
         for r in self.mats.values():
@@ -263,7 +266,9 @@ class Server:
                 self.g_dsh.copy_(self.g_hsh, non_blocking=True)
                 G.h2_group_inertia_device(self.g_dsh, ns, self.g_dc)
                 self.g_hc.copy_(self.g_dc, non_blocking=True)
+            t_w = time.perf_counter()
             self.stream.synchronize()
+            self.wait_s += time.perf_counter() - t_w
             hc = self.g_hc.numpy()
             for i, name in enumerate(self.g_order):
                 if ns[i]:
@@ -281,7 +286,9 @@ class Server:
                     if rc != 0:
                         raise RuntimeError(L.h2_last_error().decode())
                     r.h_counts[:ns].copy_(r.d_counts[:ns], non_blocking=True)
+            t_w = time.perf_counter()
             self.stream.synchronize()
+            self.wait_s += time.perf_counter() - t_w
             for name, shifts in plans.items():
                 results[name] = self.mats[name].h_counts[:len(shifts)].numpy().copy()
         for name, shifts in plans.items():
@@ -302,6 +309,7 @@ class Server:
                     still.append(req)
             r.active = still
         self.ticks += 1
+        self.host_s += time.perf_counter() - t_host
         return len(plans)
 
 
