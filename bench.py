@@ -861,7 +861,38 @@ def _serving(args):
     res.update(_serving_run(args, args.serving_rate, args.serving_s, 4242))
     if args.serving_sustain_rate > 0:
         res["sustainable"] = _serving_run(args, args.serving_sustain_rate, args.serving_sustain_s, 4343)
+    res["plain_fp64_same_matrices"] = _plain_on_serving_mix()
+    res["served_over_plain"] = res["shifts_per_s"] / res["plain_fp64_same_matrices"]["shifts_per_s"]
     return res
+
+
+def _plain_on_serving_mix():
+    """The plain FP64 path (one shift per launch sequence, 1 lane, no graph,
+    no batching) on the serving matrices: shifts/s with the shifts spread
+    evenly over the four matrices, the baseline of the served rate."""
+    import torch
+    import paper_2311_08618_gb300 as pkg
+    st = torch.cuda.Stream()
+    per = []
+    for i, n in enumerate(SERVING_SIZES):
+        M = pkg.H2Matrix(W.uniform_cube(n, 2, 100 + i), W.LAPLACE_EPS, (1e-3, 0, 0, 0), leaf=64, rank=16,
+                         max_lanes=1, stream=st.cuda_stream, graphs=0)
+        info = M.h2_info()
+        sh = torch.tensor([0.5 * (info["gershgorin_lo"] + info["gershgorin_hi"])], dtype=torch.float64, device="cuda")
+        c = torch.zeros(1, dtype=torch.int64, device="cuda")
+        for _ in range(2):
+            M.h2_inertia_device(sh, 1, c)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(4):
+            M.h2_inertia_device(sh, 1, c)
+        e1.record(st)
+        torch.cuda.synchronize()
+        per.append(e0.elapsed_time(e1) / 4)
+        M.close()
+    mean_ms = sum(per) / len(per)
+    return {"ms_per_shift": dict(zip([str(n) for n in SERVING_SIZES], per)), "shifts_per_s": 1e3 / mean_ms}
 
 
 def _ncu_case(args):
