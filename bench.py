@@ -390,6 +390,22 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
     lat = np.array(lat[2:])
     info2 = Me.h2_info()
     Me.close()
+    # latency of one k-th solve against the lanes per round: (q+1)-section
+    # needs fewer rounds with more lanes, but each round's batch takes longer
+    eig_sweep = []
+    for ln in (8, 16, 32, 64):
+        Ms = pkg.H2Matrix(X, WORKLOAD["kernel"], WORKLOAD["kparams"], leaf=WORKLOAD["leaf"], rank=WORKLOAD["rank"],
+                          eta=WORKLOAD["eta"], max_lanes=ln, stream=stream.cuda_stream)
+        ls = []
+        for i in range(5):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            Ms.h2_kth_eig([WORKLOAD["k"]], WORKLOAD["tol"])
+            ls.append(time.perf_counter() - t)
+        inf_s = Ms.h2_info()
+        eig_sweep.append({"lanes": ln, "p50_ms": float(np.percentile(ls[2:], 50) * 1e3),
+                          "rounds": inf_s["last_rounds"], "shifts": inf_s["last_shifts"]})
+        Ms.close()
     # ---- all n eigenvalues in one call (spectrum slicing with the reuse of
     # every (mu, nu) for every k, Sec. 4.2), on the throughput handle
     all_eigs = None
@@ -568,7 +584,7 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
                      "eigs_per_s": float(1.0 / np.mean(lat)),
                      "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                      "rounds": info2["last_rounds"], "shifts_per_solve": info2["last_shifts"],
-                     "lambda": lam[0], "err_bound": lam[1]},
+                     "lambda": lam[0], "err_bound": lam[1], "by_lanes": eig_sweep},
             "build_s": build_s, "roofline": roof, "clocks": clocks, "precision": precision,
             "all_eigs": all_eigs, "fp64_tc": fp64_tc, "plain_fp64": plain, "compression": compression,
             "e2_sweep": e2, "large_configs": large,
@@ -687,7 +703,7 @@ def _e2_sweep(args):
     n = 1024
     X = W.unit_circle(n, 5)
     Xt = torch.tensor(X, dtype=torch.float64, device="cuda")
-    r = torch.cdist(Xt, Xt)
+    r = torch.cdist(Xt, Xt, compute_mode="donot_use_mm_for_euclid_dist")   # exact differences: r_ii = 0
     ev = torch.linalg.eigvalsh(1.0 / (r + 1e-3)).cpu().numpy()
     del Xt, r
     st = torch.cuda.Stream()
@@ -814,15 +830,18 @@ def _batching(args):
     return res
 
 
-def _serving_run(args, rate, seconds, seed):
+def _serving_run(args, rate, seconds, seed, mats=None, lanes=None, grace_s=25.0):
     """One open-loop run on freshly built resident matrices (cold (mu, nu)
-    tables): Poisson arrivals at `rate` for `seconds`."""
+    tables): Poisson arrivals at `rate` for `seconds`.  mats: (n, d, leaf,
+    rank) per matrix, the 2D stand-in by default."""
     import paper_2311_08618_gb300 as pkg
     from paper_2311_08618_gb300 import serving
     srv = serving.Server()
-    for i, n in enumerate(SERVING_SIZES):
-        srv.add_matrix("m%d" % i, W.uniform_cube(n, 2, 100 + i), W.LAPLACE_EPS, (1e-3, 0, 0, 0), 64, 16,
-                       lanes=args.serving_lanes, precision=pkg.H2_PREC_FP64_TC)
+    mats = mats or [(n, 2, 64, 16) for n in SERVING_SIZES]
+    for i, (n, d, leaf, rank) in enumerate(mats):
+        srv.add_matrix("m%d" % i, W.uniform_cube(n, d, 100 + i), W.LAPLACE_EPS, (1e-3, 0, 0, 0), leaf, rank,
+                       lanes=lanes or args.serving_lanes, precision=pkg.H2_PREC_FP64_TC)
+    sizes = [m[0] for m in mats]
     u = W.uniform(seed, 4 * 100000)
     arr, t, j = [], 0.0, 0
     while True:
@@ -830,13 +849,13 @@ def _serving_run(args, rate, seconds, seed):
         j += 1
         if t > seconds:
             break
-        mi = int(u[j] * len(SERVING_SIZES))
-        k = 1 + int(u[j + 1] * SERVING_SIZES[mi])
+        mi = int(u[j] * len(sizes))
+        k = 1 + int(u[j + 1] * sizes[mi])
         tol = 10.0 ** (-10.0 + 4.0 * u[j + 2])
         j += 3
         arr.append((t, "m%d" % mi, k, tol))
     t0 = time.perf_counter()
-    done, unfinished = serving.run_open_loop(srv, arr, seconds, deadline_s=seconds + 25.0)
+    done, unfinished = serving.run_open_loop(srv, arr, seconds, deadline_s=seconds + grace_s)
     wall = time.perf_counter() - t0
     res = {"arrivals": "Poisson %.0f q/s for %.0f s" % (rate, seconds), "offered": len(arr),
            "completed": len(done), "unfinished": unfinished, "wall_s": wall,
@@ -863,6 +882,12 @@ def _serving(args):
         res["sustainable"] = _serving_run(args, args.serving_sustain_rate, args.serving_sustain_s, 4343)
     res["plain_fp64_same_matrices"] = _plain_on_serving_mix()
     res["served_over_plain"] = res["shifts_per_s"] / res["plain_fp64_same_matrices"]["shifts_per_s"]
+    if args.serving_3d_s > 0:
+        r3 = {"matrices": "2 resident 3D 1/(r+1e-3) H2 matrices n=16384 (leaf 256, rank 32: the serving "
+                          "configuration's shape), 8 lanes each, FP64_TC"}
+        r3.update(_serving_run(args, args.serving_3d_rate, args.serving_3d_s, 4444,
+                               mats=[(16384, 3, 256, 32), (16384, 3, 256, 32)], lanes=8, grace_s=60.0))
+        res["serving_3d"] = r3
     return res
 
 
@@ -949,6 +974,8 @@ def main():
     ap.add_argument("--batch-nmax", type=int, default=8192)
     ap.add_argument("--batch-lanes", type=int, default=4)
     ap.add_argument("--serving-lanes", type=int, default=16)
+    ap.add_argument("--serving-3d-s", type=float, default=10.0, help="seconds of arrivals, 3D serving (0: skip)")
+    ap.add_argument("--serving-3d-rate", type=float, default=0.5)
     ap.add_argument("--workload", default="laplace2d_n1024", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1], help="0 FP64, 1 mixed (main handle)")
     ap.add_argument("--ncu-case", default="", choices=["", "fp64", "mixed", "fp64_tc", "fp64_tc_tcgen05"],
