@@ -126,6 +126,17 @@ typedef struct {
                             elimination's stacked targets), 0 (default) =
                             warp-level mma.sync tiles of 32 x 32.  Both give the
                             same values */
+    int lookahead;       /* 1: within a level, once colour c's Schur updates
+                            of the blocks in rows and columns of colour c + 1's
+                            clusters are done, colour c + 1's recompression,
+                            rotation, LDL^T and solves run on a second stream
+                            beside colour c's remaining updates (graph-replayed
+                            batches of the handle's own shifts; each block
+                            takes its updates in the same order, so the results
+                            are the same bit for bit; twice the factor-step
+                            scratch); 0 (default): one stream, colour after
+                            colour, which measured faster (the concurrent
+                            Schur blocks slow the solves on the critical path) */
 } h2_options;
 
 /* Fills *opt with the defaults above.  Never fails. */

@@ -44,6 +44,7 @@ void h2_default_options(h2_options* opt) {
     opt->stream = nullptr;
     opt->graphs = 1;
     opt->tc_schur = 0;
+    opt->lookahead = 0;
 }
 
 const char* h2_last_error(void) { return g_last_error.c_str(); }

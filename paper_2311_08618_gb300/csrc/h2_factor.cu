@@ -2435,6 +2435,10 @@ struct ColourDev {
     int *cl, *targ, *targ_slot, *targ_trans, *ntarg, *rowblk, *rowblk_other, *rowblk_trans, *rowblk_fill,
         *nrow, *fillq, *fillslot, *nfill;
     SchurPair* pairs;
+    // lookahead schedule: the pairs whose block lies in a row or column of a
+    // cluster of the next colour (A), and the rest (B), in their list order
+    SchurPair *pairsA, *pairsB;
+    int npairsA, npairsB;
 };
 
 struct LevelWork {
@@ -2475,6 +2479,9 @@ struct FactorState {
     int* d_rr_idx = nullptr;      // [lanes]
     int* d_rr_n = nullptr;        // [1]
     unsigned long long* d_tally = nullptr;   // [2]: shifts checked, shifts re-run in FP64
+    // lookahead schedule: the second stream of the fork and its two events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // device-resident bisection loop (graph with a conditional WHILE node)
     KthLoop* d_loop = nullptr;
     cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};   // [mixed]
@@ -2501,6 +2508,10 @@ static bool use_graphs(const h2_matrix* h) {
     return !no_graph && h->opt.graphs != 0;
 }
 int heartbeat_setup();
+
+// the lookahead schedule (h2_options.lookahead) applies to a handle's own
+// graph-replayed batches
+static bool lookahead_on(const h2_matrix* h) { return h->opt.lookahead != 0 && use_graphs(h); }
 
 // padded block dimension of every level (leaves: the largest leaf; above:
 // twice the children's skeleton cap)
@@ -2554,7 +2565,7 @@ size_t workspace_lane_bytes(h2_matrix* h) {
         size_t ncl_max = 0;
         for (const auto& cl : lp.color_lists) ncl_max = std::max(ncl_max, cl.size());
         slots += (size_t)std::max(D.nslots, 1) * D.dmax * D.dmax * 8 + (size_t)D.nc * 8;
-        scratch = std::max(scratch, ncl_max * lay.total * 8);
+        scratch = std::max(scratch, ncl_max * lay.total * 8 * (lookahead_on(h) ? 2 : 1));
         if (l < P.L) merge = std::max(merge, (size_t)D.nslots * 2 * D.dmax * D.dmax * 8);
     }
     return slots + scratch + merge + 5 * 8;
@@ -2646,6 +2657,17 @@ int alloc_workspace(h2_matrix* h, int lanes) {
                 if (nfl > 0) C.has_fill = 1;
             }
             C.npairs = (int)pairs.size();
+            {
+                const size_t ci_now = W.colours.size();
+                std::vector<char> in_next(nc, 0);
+                if (ci_now + 1 < lp.color_lists.size())
+                    for (int q : lp.color_lists[ci_now + 1]) in_next[q] = 1;
+                std::vector<SchurPair> pa, pb;
+                for (const SchurPair& sp : pairs) (in_next[sp.a] || in_next[sp.b] ? pa : pb).push_back(sp);
+                C.npairsA = (int)pa.size();
+                C.npairsB = (int)pb.size();
+                if ((rc = upload(&C.pairsA, pa)) || (rc = upload(&C.pairsB, pb))) return rc;
+            }
             if ((rc = upload(&C.cl, std::vector<int>(cl.begin(), cl.end()))) || (rc = upload(&C.targ, targ)) ||
                 (rc = upload(&C.targ_slot, tslot)) || (rc = upload(&C.targ_trans, ttr)) ||
                 (rc = upload(&C.ntarg, ntarg)) || (rc = upload(&C.rowblk, rowblk)) ||
@@ -2683,9 +2705,17 @@ int alloc_workspace(h2_matrix* h, int lanes) {
         if ((rc = dalloc(&ws.d_rk[l], (size_t)D.nc * lanes))) return rc;
         bytes += sz * 8 + (size_t)D.nc * lanes * 8;
     }
-    if ((rc = dalloc(&ws.d_scratch, scratch_max))) return rc;
+    // the lookahead schedule runs colour c + 1's solves while colour c's Schur
+    // updates read their factors: two scratch halves, by colour parity
+    ws.scratch_half = scratch_max;
+    if ((rc = dalloc(&ws.d_scratch, (lookahead_on(h) ? 2 : 1) * scratch_max))) return rc;
+    if (lookahead_on(h)) {
+        CK(cudaStreamCreateWithFlags(&fs->side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&fs->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&fs->ev_join, cudaEventDisableTiming));
+    }
     if ((rc = dalloc(&ws.d_merge, std::max<size_t>(merge_max, 1)))) return rc;
-    bytes += (scratch_max + merge_max) * 8;
+    bytes += ((lookahead_on(h) ? 2 : 1) * scratch_max + merge_max) * 8;
     if ((rc = dalloc(&ws.d_neg, lanes)) || (rc = dalloc(&ws.d_minpiv, lanes)) || (rc = dalloc(&ws.d_err, 8)) ||
         (rc = dalloc(&ws.d_shifts, lanes)) || (rc = dalloc(&fs->d_active, 1)) ||
         (rc = dalloc(&fs->d_counts, lanes)) || (rc = dalloc(&fs->d_mp, lanes)) ||
@@ -2734,7 +2764,7 @@ struct Profiler {
 // launch (h2_group).  The 1-D bookkeeping kernels are kept as closures.
 enum Op {
     OP_INIT_DIMS, OP_INIT_LEAF, OP_RECOMP, OP_RECOMP_CL, OP_ROTATE, OP_LDL, OP_TRSM, OP_SCHUR,
-    OP_MERGE_DIMS, OP_MERGE, OP_FINISH
+    OP_MERGE_DIMS, OP_MERGE, OP_FINISH, OP_FORK, OP_JOIN
 };
 
 struct LaunchRec {
@@ -2745,6 +2775,7 @@ struct LaunchRec {
     int block = NT;
     size_t smem = 0;
     int flag = 0;
+    int branch = 0;                        // lookahead schedule: 1 = the side stream
     FactorArgs fa{};
     SchurArgs sa{};
     InitArgs ia{};
@@ -2764,7 +2795,7 @@ static bool recomp_clustered(const h2_matrix* h, int l, int nfill_max, int Dm) {
     return wide >= 0 && (size_t)nfill_max * Dm >= (wide > 0 ? (size_t)wide : kWideFill);
 }
 
-static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
+static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed, bool lookahead = false) {
     std::vector<LaunchRec> R;
     const Plan& P = h->plan;
     const int L = P.L;
@@ -2804,12 +2835,22 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
         LevelDev& D = h->lev[l];
         LevelWork& W = fs->lw[l];
         const int Dm = D.dmax;
-        for (int c = 0; c < (int)W.colours.size(); ++c) {
+        const int ncol = (int)W.colours.size();
+        // the records of colour c: its chain (recompression, rotation, LDL^T,
+        // solves) and its Schur update, whole and split into the pairs in rows
+        // and columns of the next colour's clusters (A) and the others (B)
+        struct ColourRecs {
+            std::vector<LaunchRec> chain;
+            LaunchRec schur, schurA, schurB;
+        };
+        auto colour_recs = [&](int c) {
+            ColourRecs out;
             const ColourDev& C = W.colours[c];
+            double* scr = ws.d_scratch + ((lookahead && (c & 1)) ? ws.scratch_half : 0);
             FactorArgs fa{ws.d_slots[l], D.dmax, LN, ws.d_dim[l], ws.d_rk[l], D.d_color, c, C.cl, C.targ,
                           C.targ_slot, C.targ_trans, C.ntarg, C.ntarg_max, C.rowblk, C.rowblk_other,
                           C.rowblk_trans, C.rowblk_fill, C.nrow, C.nrow_max, C.fillq, C.fillslot, C.nfill,
-                          C.nfill_max, ws.d_scratch, W.lay, h->tol, 2.220446049250313e-16 * h->norm_inf,
+                          C.nfill_max, scr, W.lay, h->tol, 2.220446049250313e-16 * h->norm_inf,
                           h->fill_cap_eff, ws.d_neg, ws.d_minpiv, ws.d_err, fs->d_active, fs->d_stats, C.ncl};
             LaunchRec r;
             r.phase = 2;
@@ -2827,7 +2868,7 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
                     q.op = OP_RECOMP;
                     q.grid = dim3(C.ncl, LN);
                 }
-                R.push_back(q);
+                out.chain.push_back(q);
                 q = r;
                 q.op = OP_ROTATE;
                 q.kind = H2_KIND_ROTATE;
@@ -2842,7 +2883,7 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
                     q.variant = rotate_nu(Dm);
                     q.smem = rotate_smem<float>(Dm);
                 }
-                R.push_back(q);
+                out.chain.push_back(q);
             }
             {
                 const size_t sm_ldl = ((size_t)Dm * Dm + 4 * (size_t)Dm) * sizeof(double);
@@ -2861,7 +2902,7 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
                     q.smem = q.flag ? sm_ldl : 0;
                     q.grid = dim3(C.ncl, LN);
                 }
-                R.push_back(q);
+                out.chain.push_back(q);
             }
             {
                 // flags 0 and 1: Rp pivot reciprocals, then (flag 1) L and the pivots
@@ -2877,7 +2918,7 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
                 q.variant = mixed ? 1 : 0;
                 q.smem = q.flag == 2 ? sm_full : (q.flag ? sm_trsm : sm_rc);
                 q.grid = dim3(C.ncl * C.ntarg_max, LN);
-                R.push_back(q);
+                out.chain.push_back(q);
             }
             {
                 const int ts = mixed ? TSF : TS;
@@ -2886,7 +2927,7 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
                 LaunchRec q = r;
                 q.op = OP_SCHUR;
                 q.kind = H2_KIND_SCHUR;
-                q.sa = SchurArgs{ws.d_slots[l], D.dmax, LN, C.pairs, tdim * tdim, tdim, ws.d_scratch, W.lay,
+                q.sa = SchurArgs{ws.d_slots[l], D.dmax, LN, C.pairs, tdim * tdim, tdim, scr, W.lay,
                                  fs->d_active, ws.d_err, C.ntarg, npanel};
                 q.variant = mixed ? 1 : (h->opt.precision == H2_PREC_FP64_TC ? 2 : 0);
                 q.grid = dim3(C.npairs * tdim * tdim, LN);
@@ -2898,7 +2939,48 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed) {
                     q.smem = TC_SMEM;
                     q.grid = dim3(C.ncl * npanel, LN);
                 }
-                R.push_back(q);
+                out.schur = q;
+                out.schurA = q;
+                out.schurA.sa.pairs = C.pairsA;
+                out.schurA.grid = dim3(C.npairsA * tdim * tdim, LN);
+                out.schurB = q;
+                out.schurB.sa.pairs = C.pairsB;
+                out.schurB.grid = dim3(C.npairsB * tdim * tdim, LN);
+                out.schurB.branch = 1;
+            }
+            return out;
+        };
+        if (!lookahead) {
+            for (int c = 0; c < ncol; ++c) {
+                ColourRecs cr = colour_recs(c);
+                for (auto& q : cr.chain) R.push_back(q);
+                R.push_back(cr.schur);
+            }
+        } else {
+            // the lookahead schedule: after colour c's Schur updates in the next
+            // colour's rows and columns, colour c + 1's chain runs on the main
+            // stream while the rest of colour c's Schur updates run on the side
+            // stream; every block still takes its updates in the same order
+            std::vector<ColourRecs> crs;
+            for (int c = 0; c < ncol; ++c) crs.push_back(colour_recs(c));
+            for (auto& q : crs[0].chain) R.push_back(q);
+            for (int c = 0; c < ncol; ++c) {
+                const bool split = c + 1 < ncol && crs[c].schur.variant != 3;
+                if (!split) {
+                    R.push_back(crs[c].schur);
+                    if (c + 1 < ncol)
+                        for (auto& q : crs[c + 1].chain) R.push_back(q);
+                    continue;
+                }
+                if (crs[c].schurA.grid.x > 0) R.push_back(crs[c].schurA);
+                LaunchRec fk;
+                fk.op = OP_FORK;
+                R.push_back(fk);
+                if (crs[c].schurB.grid.x > 0) R.push_back(crs[c].schurB);
+                for (auto& q : crs[c + 1].chain) R.push_back(q);
+                LaunchRec jn;
+                jn.op = OP_JOIN;
+                R.push_back(jn);
             }
         }
         if (l > 0) {
@@ -2981,12 +3063,27 @@ static void launch_single(const LaunchRec& r, cudaStream_t st) {
 
 // enqueue one full factorization of the workspace's lanes on stream st;
 // returns the number of kernel launches
-static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, int mixed) {
+// Enqueues one batch's kernels on st.  With lookahead (graph captures only),
+// the side-branch records go to the handle's second stream between a fork
+// (st's progress recorded, the side stream waits for it) and a join (the side
+// stream's progress recorded, st waits for it).
+static int enqueue_factorization(h2_matrix* h, cudaStream_t st, Profiler* prof, int mixed, bool lookahead = false) {
+    FactorState* fs = state_of(h);
     int nl = 0;
-    for (const LaunchRec& r : factor_records(h, mixed)) {
+    for (const LaunchRec& r : factor_records(h, mixed, lookahead)) {
+        if (r.op == OP_FORK) {
+            CK(cudaEventRecord(fs->ev_fork, st));
+            CK(cudaStreamWaitEvent(fs->side, fs->ev_fork, 0));
+            continue;
+        }
+        if (r.op == OP_JOIN) {
+            CK(cudaEventRecord(fs->ev_join, fs->side));
+            CK(cudaStreamWaitEvent(st, fs->ev_join, 0));
+            continue;
+        }
         ++nl;
         if (prof) prof->before(r.kind);
-        launch_single(r, st);
+        launch_single(r, r.branch ? fs->side : st);
         if (prof) prof->after();
     }
     return nl;
@@ -3356,7 +3453,7 @@ static int ensure_graph(h2_matrix* h, int mixed) {
     cudaStream_t st = h->stream;
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    h->kernels_per_batch = enqueue_factorization(h, st, nullptr, mixed);
+    h->kernels_per_batch = enqueue_factorization(h, st, nullptr, mixed, lookahead_on(h));
     CK(cudaStreamEndCapture(st, &g));
     CK(cudaGraphInstantiate(&ge, g, 0));
     cudaGraphDestroy(g);
@@ -3780,7 +3877,7 @@ static int build_loop_graph(h2_matrix* h, int mixed) {
     CK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     k_bisect_plan_loop<<<1, 1024, 0, st>>>(fs->d_lo, fs->d_hi, fs->d_loop, ws.lanes, ws.d_shifts, fs->d_active,
                                            fs->d_nact, fs->d_first, cond);
-    enqueue_factorization(h, st, nullptr, mixed);
+    enqueue_factorization(h, st, nullptr, mixed, lookahead_on(h));
     k_bisect_update_loop<<<(unsigned)((fs->nk_cap + 127) / 128), 128, 0, st>>>(
         fs->d_lo, fs->d_hi, fs->d_k, fs->d_loop, ws.d_shifts, fs->d_counts, fs->d_active);
     cudaGraph_t captured;
@@ -3984,6 +4081,7 @@ void free_workspace(h2_matrix* h) {
                 cudaFree(C.ntarg); cudaFree(C.rowblk); cudaFree(C.rowblk_other); cudaFree(C.rowblk_trans);
                 cudaFree(C.rowblk_fill);
                 cudaFree(C.nrow); cudaFree(C.fillq); cudaFree(C.fillslot); cudaFree(C.nfill); cudaFree(C.pairs);
+                cudaFree(C.pairsA); cudaFree(C.pairsB);
             }
             cudaFree(W.d_slot_of); cudaFree(W.d_far_of);
         }
@@ -3994,6 +4092,9 @@ void free_workspace(h2_matrix* h) {
         cudaFree(fs->d_loop);
         for (auto& e : fs->loop_exec)
             if (e) cudaGraphExecDestroy(e);
+        if (fs->side) cudaStreamDestroy(fs->side);
+        if (fs->ev_fork) cudaEventDestroy(fs->ev_fork);
+        if (fs->ev_join) cudaEventDestroy(fs->ev_join);
         delete fs;
     }
     ws.graph_state = nullptr;

@@ -103,7 +103,8 @@ struct Workspace {
     std::vector<double*> d_slots;  // per level [nslots][lanes][dmax*dmax]
     std::vector<int*> d_dim;       // per level [nc][lanes]
     std::vector<int*> d_rk;        // per level [nc][lanes]
-    double* d_scratch = nullptr;   // factor-step scratch
+    double* d_scratch = nullptr;   // factor-step scratch (two halves with the lookahead schedule)
+    size_t scratch_half = 0;       // doubles of one half
     size_t scratch_per_elim = 0;   // doubles per (cluster, lane)
     double* d_merge = nullptr;     // merge scratch
     size_t merge_doubles = 0;
