@@ -432,6 +432,304 @@ __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, doubl
     __syncthreads();
 }
 
+// Ordering key of |x|: the bit pattern of a non-negative double, read as an
+// unsigned integer, orders like its value (a NaN ranks above +inf).  Pivot
+// searches compare these keys in the integer pipes.
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// Block argmax of (key, index): the largest key, the smallest index on ties,
+// the same on every thread.  Within a warp three integer reductions (high
+// word, low word among the maxima, index among the exact maxima); across
+// warps one barrier and a scan of the warps' winners.  bk / bi: 2 * NTH / 32
+// entries each, double-buffered by par like block_argmax1.
+template <int NTH>
+__device__ __forceinline__ int block_argmax_key(unsigned long long key, int idx, unsigned long long* bk, int* bi,
+                                                int par, unsigned long long* out_key) {
+    constexpr int NW = NTH / 32;
+    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    const unsigned mi = __reduce_min_sync(0xffffffffu, (hi == mh && lo == ml) ? (unsigned)idx : 0xffffffffu);
+    unsigned long long* k2 = bk + par * NW;
+    int* i2 = bi + par * NW;
+    if ((threadIdx.x & 31) == 0) {
+        k2[threadIdx.x >> 5] = ((unsigned long long)mh << 32) | ml;
+        i2[threadIdx.x >> 5] = (int)min(mi, 0x7fffffffu);
+    }
+    __syncthreads();
+    unsigned long long kb = k2[0];
+    int ib = i2[0];
+#pragma unroll
+    for (int u = 1; u < NW; ++u) {
+        const unsigned long long ku = k2[u];
+        const int iu = i2[u];
+        if (ku > kb || (ku == kb && iu < ib)) { kb = ku; ib = iu; }
+    }
+    *out_key = kb;
+    return ib;
+}
+
+// S[i][j] -= a_i b_j (+ a2_i b2_j) over the lower triangle o <= j <= i < n of
+// a row-major block.  The rows are taken in folded pairs (o + q, n - 1 - q),
+// whose q + 1 and n - o - q entries make one span of n - o + 1 (the middle
+// row of an odd count alone); warp w takes spans w, w + NW, ... and its lanes
+// walk the span, so every warp gets about the same number of elements.
+template <bool TWO, int NW>
+__device__ __forceinline__ void lower_rank_update(double* S, int lds, int o, int n, const double* a, const double* b,
+                                                  const double* a2, const double* b2) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = n - o;
+    const int P = (t + 1) >> 1;
+    for (int q = warp; q < P; q += NW) {
+        const int ra = o + q, rb = n - 1 - q;
+        const int len = ra == rb ? q + 1 : t + 1;
+        for (int m = lane; m < len; m += 32) {
+            const int i = m <= q ? ra : rb;
+            const int j = m <= q ? o + m : o + m - q - 1;
+            double v = S[(size_t)i * lds + j];
+            if (TWO) v -= a[i] * b[j] + a2[i] * b2[j];
+            else v -= a[i] * b[j];
+            S[(size_t)i * lds + j] = v;
+        }
+    }
+}
+
+// |x| (given by its key) as a float scaled by 2^(1023 - eref), eref being the
+// biased exponent of the largest value it is compared with; the mantissa is
+// truncated to 23 bits and values below 2^-126 of the reference read as 0.
+// Integer operations only.
+__device__ __forceinline__ float key_scaled(unsigned long long key, int eref) {
+    const int e = (int)(key >> 52) - eref + 127;
+    if (e <= 0) return 0.0f;
+    return __uint_as_float(((unsigned)e << 23) | ((unsigned)(key >> 29) & 0x7fffffu));
+}
+
+// Bunch-Kaufman LDL^T of an n x n symmetric block on one CTA of NTH threads,
+// reading and updating only the lower triangle and diagonal of S (the strict
+// upper triangle is neither read nor written).  The output is cta_bk_ldl's
+// packed factor (L strictly below the diagonal except the (k + 1, k) entry of
+// a 2x2 pivot, which holds D's off-diagonal; D on the diagonal; perm, piv).
+//
+// On this GPU an FP64 instruction of a warp holds its sub-partition's FP64
+// unit for many cycles, and a pivot step is a chain of dependent scalar
+// operations, so the FP64 work is kept off that chain where exactness does
+// not need it:
+//   - the pivot searches compare |values| as integer keys (largest value,
+//     first index on ties; a NaN ranks largest and flags *bad);
+//   - the test |a_kk| >= alpha lambda (alpha = (1 + sqrt 17) / 8) is made
+//     on 24-bit scaled copies of the two values (the threshold moves by at
+//     most 2^-23 relative); the tests of a pivoting step (after the search
+//     of column r) stay in FP64;
+//   - the negative count and the smallest |pivot| are formed after the loop,
+//     one pivot block per thread;
+//   - the trailing update touches the triangle only (half of cta_bk_ldl's
+//     products), balanced across the warps.
+// Keep lds odd when S is in shared memory: the column reads of the pivot
+// search are then free of bank conflicts.  rk / ri: 2 * NTH / 32 entries
+// each; buf: 4n values.  neg / minpiv / bad: thread 0 accumulates.
+template <int NTH>
+__device__ void cta_bk_ldl_lower(double* S, int lds, int n, int* perm, int* piv, unsigned long long* rk, int* ri,
+                                 int* neg, double* minpiv, int* bad, double zero_pivot, double* buf) {
+    constexpr int NW = NTH / 32;
+    constexpr unsigned long long kInf = 0x7ff0000000000000ull;
+    const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+    const float alpha_f = 0.640388203f;   // alpha rounded to FP32
+    const int tid = threadIdx.x;
+    const bool zp = zero_pivot != 0.0;
+    double* c0 = buf;
+    double* c1 = buf + n;
+    double* l0 = buf + 2 * n;
+    double* l1 = buf + 3 * n;
+    for (int i = tid; i < n; i += NTH) perm[i] = i;
+    __syncthreads();
+    int k = 0, par = 0, flag_nan = 0;
+    while (k < n) {
+        const unsigned long long akey = abs_key(S[(size_t)k * lds + k]);
+        unsigned long long key = 0;
+        int bi = 0x7fffffff;
+        for (int i = k + 1 + tid; i < n; i += NTH) {
+            const unsigned long long v = abs_key(S[(size_t)i * lds + k]);
+            if (v > key) { key = v; bi = i; }
+        }
+        unsigned long long lk;
+        int r = block_argmax_key<NTH>(key, bi, rk, ri, par, &lk);
+        par ^= 1;
+        if (k + 1 >= n) { lk = 0; r = k; }
+        else if (r <= k || r >= n) r = k + 1;
+        int size = 1;
+        int swap_a = -1, swap_b = -1;
+        bool test = false;
+        if (akey > kInf || lk > kInf) {
+            flag_nan = 1;   // NaN: finish with 1x1 steps, flagged
+        } else if (lk != 0) {
+            const int eref = (int)(max(akey, lk) >> 52);
+            test = !(key_scaled(akey, eref) >= alpha_f * key_scaled(lk, eref));
+        }
+        if (test) {
+            // sig = max_{j >= k, j != r} |S_jr| from the lower triangle
+            const double akk = __longlong_as_double((long long)akey), lam = __longlong_as_double((long long)lk);
+            const double arr = __longlong_as_double((long long)abs_key(S[(size_t)r * lds + r]));
+            key = 0;
+            bi = 0x7fffffff;
+            for (int j = k + tid; j < n; j += NTH) {
+                if (j == r) continue;
+                const unsigned long long v = abs_key(j > r ? S[(size_t)j * lds + r] : S[(size_t)r * lds + j]);
+                if (v > key) { key = v; bi = j; }
+            }
+            unsigned long long sk;
+            block_argmax_key<NTH>(key, bi, rk, ri, par, &sk);
+            par ^= 1;
+            const double sig = __longlong_as_double((long long)sk);
+            if (akk * sig >= alpha * lam * lam) {
+                // 1x1 at k
+            } else if (arr >= alpha * sig) {
+                swap_a = k; swap_b = r;
+            } else {
+                swap_a = k + 1; swap_b = r;
+                size = 2;
+            }
+        }
+        if (swap_a >= 0 && swap_a != swap_b) {
+            // symmetric interchange of sa < sb in lower-triangle storage
+            const int sa = swap_a, sb = swap_b;
+            __syncthreads();   // every thread has read S for the searches
+            for (int j = tid; j < sa; j += NTH) {
+                const double t = S[(size_t)sa * lds + j];
+                S[(size_t)sa * lds + j] = S[(size_t)sb * lds + j];
+                S[(size_t)sb * lds + j] = t;
+            }
+            for (int i = sa + 1 + tid; i < sb; i += NTH) {
+                const double t = S[(size_t)i * lds + sa];
+                S[(size_t)i * lds + sa] = S[(size_t)sb * lds + i];
+                S[(size_t)sb * lds + i] = t;
+            }
+            for (int i = sb + 1 + tid; i < n; i += NTH) {
+                const double t = S[(size_t)i * lds + sa];
+                S[(size_t)i * lds + sa] = S[(size_t)i * lds + sb];
+                S[(size_t)i * lds + sb] = t;
+            }
+            if (tid == 0) {
+                const double t = S[(size_t)sa * lds + sa];
+                S[(size_t)sa * lds + sa] = S[(size_t)sb * lds + sb];
+                S[(size_t)sb * lds + sb] = t;
+                const int q = perm[sa];
+                perm[sa] = perm[sb];
+                perm[sb] = q;
+            }
+            __syncthreads();
+        }
+        if (size == 1) {
+            double d = S[(size_t)k * lds + k];
+            const bool dz = abs_key(d) == 0;
+            if (dz && zp) d = zero_pivot;   // zero column: stored as zero_pivot
+            const bool elim = !(dz && !zp) && k + 1 < n;
+            if (elim) {
+                const double invd = 1.0 / d;
+                for (int i = k + 1 + tid; i < n; i += NTH) {
+                    const double c = S[(size_t)i * lds + k];
+                    const double l = c * invd;
+                    c0[i] = c;
+                    l0[i] = l;
+                    S[(size_t)i * lds + k] = l;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                S[(size_t)k * lds + k] = d;
+                piv[k] = 1;
+            }
+            if (elim) {
+                lower_rank_update<false, NW>(S, lds, k + 1, n, l0, c0, nullptr, nullptr);
+                __syncthreads();
+            }
+            k += 1;
+        } else {
+            const double a = S[(size_t)k * lds + k], b = S[(size_t)(k + 1) * lds + k],
+                         c = S[(size_t)(k + 1) * lds + k + 1];
+            if (k + 2 < n) {
+                const double det = a * c - b * b;
+                const double idet = 1.0 / det;
+                const double i00 = c * idet, i01 = -b * idet, i11 = a * idet;
+                for (int i = k + 2 + tid; i < n; i += NTH) {
+                    const double ci0 = S[(size_t)i * lds + k], ci1 = S[(size_t)i * lds + k + 1];
+                    const double a0 = ci0 * i00 + ci1 * i01, a1 = ci0 * i01 + ci1 * i11;
+                    c0[i] = ci0;
+                    c1[i] = ci1;
+                    l0[i] = a0;
+                    l1[i] = a1;
+                    S[(size_t)i * lds + k] = a0;
+                    S[(size_t)i * lds + k + 1] = a1;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                piv[k] = 2;
+                piv[k + 1] = 0;
+            }
+            if (k + 2 < n) {
+                lower_rank_update<true, NW>(S, lds, k + 2, n, l0, c0, l1, c1);
+                __syncthreads();
+            }
+            k += 2;
+        }
+    }
+    __syncthreads();
+    // the inertia of D and its smallest |eigenvalue|, one pivot block per
+    // thread: a 1x1 pivot d counts if d < 0; a 2x2 block [a b; b c] has one
+    // negative eigenvalue if det < 0, two if det >= 0 and a + c < 0
+    int nn = 0, nb = 0;
+    unsigned long long mk = kInf;
+    for (int j = tid; j < n; j += NTH) {
+        const int pv = piv[j];
+        if (pv == 1) {
+            const double d = S[(size_t)j * lds + j];
+            const unsigned long long dk = abs_key(d);
+            nn += (__double_as_longlong(d) < 0 && dk != 0 && dk <= kInf) ? 1 : 0;
+            if (dk > kInf) nb = 1;
+            mk = min(mk, dk);
+        } else if (pv == 2) {
+            const double a = S[(size_t)j * lds + j], b = S[(size_t)(j + 1) * lds + j],
+                         c = S[(size_t)(j + 1) * lds + j + 1];
+            const double det = a * c - b * b, tr = a + c;
+            nn += det < 0.0 ? 1 : (tr < 0.0 ? 2 : 0);
+            const double disc = sqrt(fmax(0.0, 0.25 * (a - c) * (a - c) + b * b));
+            const double e0 = 0.5 * tr - disc, e1 = 0.5 * tr + disc;
+            mk = min(mk, min(abs_key(e0), abs_key(e1)));
+            if (det != det) nb = 1;
+        }
+    }
+    nn = __reduce_add_sync(0xffffffffu, nn);
+    nb = __reduce_or_sync(0xffffffffu, nb);
+    {
+        const unsigned hi = (unsigned)(mk >> 32), lo = (unsigned)mk;
+        const unsigned mh = __reduce_min_sync(0xffffffffu, hi);
+        const unsigned ml = __reduce_min_sync(0xffffffffu, hi == mh ? lo : 0xffffffffu);
+        mk = ((unsigned long long)mh << 32) | ml;
+    }
+    unsigned long long* k2 = rk + par * NW;
+    int* i2 = ri + par * NW;
+    if ((tid & 31) == 0) {
+        k2[tid >> 5] = mk;
+        i2[tid >> 5] = nn | (nb << 30);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int tn = 0, tb = flag_nan;
+        unsigned long long tm = kInf;
+        for (int u = 0; u < NW; ++u) {
+            tn += i2[u] & 0x3fffffff;
+            tb |= i2[u] >> 30;
+            tm = min(tm, k2[u]);
+        }
+        *neg += tn;
+        *minpiv = fmin(*minpiv, __longlong_as_double((long long)tm));
+        if (tb) *bad = 1;
+    }
+    __syncthreads();
+}
+
 // argmax over a warp: the largest v, the smallest index on ties
 __device__ __forceinline__ void warp_argmax(double& v, int& idx) {
     for (int o = 16; o > 0; o >>= 1) {

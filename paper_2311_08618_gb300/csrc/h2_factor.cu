@@ -1067,8 +1067,8 @@ __device__ __forceinline__ void k_ldl_body(const FactorArgs& A, const int use_sm
     const int ci = bx, lane = by;
     if (lane >= *A.active) return;
     extern __shared__ double sF[];
-    __shared__ double red[32];
-    __shared__ int redi[32];
+    __shared__ unsigned long long rkey[2 * NTH / 32];
+    __shared__ int ridx[2 * NTH / 32];
     __shared__ int s_neg, s_bad;
     __shared__ double s_mp;
     const int D = A.D, LN = A.lanes;
@@ -1098,18 +1098,19 @@ __device__ __forceinline__ void k_ldl_body(const FactorArgs& A, const int use_sm
     int* piv = perm + D;
     const double* Bpp = slot_ptr(A.slots, A.targ_slot[ci * A.ntarg_max], LN, lane, D);   // target 0 = p
     double* S = use_smem ? sF : F;
-    const int lds = use_smem ? Rp : D;
-    double* bkbuf = use_smem ? sF + (size_t)Rp * Rp : scr + A.lay.tmp;   // 4 Rp <= D*D doubles
-    for (int e = threadIdx.x; e < Rp * Rp; e += NTH) {
+    // odd leading dimension in shared memory (conflict-free column reads)
+    const int lds = use_smem ? (Rp | 1) : D;
+    double* bkbuf = use_smem ? sF + (size_t)Rp * lds : scr + A.lay.tmp;   // 4 Rp <= D*D doubles
+    for (int e = threadIdx.x; e < Rp * Rp; e += NTH) {      // lower triangle and diagonal
         int i = e / Rp, j = e % Rp;
-        S[(size_t)i * lds + j] = Bpp[(size_t)(rk1 + i) * D + rk1 + j];
+        if (j <= i) S[(size_t)i * lds + j] = Bpp[(size_t)(rk1 + i) * D + rk1 + j];
     }
     __syncthreads();
-    cta_bk_ldl<NTH>(S, lds, Rp, perm, piv, red, redi, &s_neg, &s_mp, &s_bad, A.zero_pivot, bkbuf);
+    cta_bk_ldl_lower<NTH>(S, lds, Rp, perm, piv, rkey, ridx, &s_neg, &s_mp, &s_bad, A.zero_pivot, bkbuf);
     if (use_smem)
         for (int e = threadIdx.x; e < Rp * Rp; e += NTH) {
             int i = e / Rp, j = e % Rp;
-            F[(size_t)i * D + j] = S[(size_t)i * lds + j];
+            if (j <= i) F[(size_t)i * D + j] = S[(size_t)i * lds + j];
         }
     if (threadIdx.x == 0) {
         atomicAdd(&A.neg[lane], (unsigned long long)s_neg);
@@ -2787,7 +2788,7 @@ struct LaunchRec {
 // fixed rules (128 threads for blocks up to 64, clusters for wide Z)
 static int ldl_threads(const h2_matrix* h, int l, int Dm) {
     if (l < (int)h->tune_ldl.size() && h->tune_ldl[l] > 0) return (h->tune_ldl[l] == 32 && Dm > 64) ? NT : h->tune_ldl[l];
-    return Dm <= 64 ? 32 : NT;
+    return Dm <= 64 ? 128 : NT;
 }
 static bool recomp_clustered(const h2_matrix* h, int l, int nfill_max, int Dm) {
     if (l < (int)h->tune_recomp.size() && h->tune_recomp[l] >= 0) return h->tune_recomp[l] == 1;
@@ -2886,7 +2887,7 @@ static std::vector<LaunchRec> factor_records(h2_matrix* h, int mixed, bool looka
                 out.chain.push_back(q);
             }
             {
-                const size_t sm_ldl = ((size_t)Dm * Dm + 4 * (size_t)Dm) * sizeof(double);
+                const size_t sm_ldl = ((size_t)Dm * (Dm + 1) + 4 * (size_t)Dm) * sizeof(double);
                 LaunchRec q = r;
                 q.op = OP_LDL;
                 q.kind = H2_KIND_LDL;
