@@ -247,22 +247,58 @@ __device__ int cta_pivqr(double* Y, int ldy, int m, int s, double tol, int cap, 
 }
 
 // Q = H_0 H_1 ... H_{k-1} (m x m, row-major, leading dimension ldq) from the
-// reflectors stored by cta_pivqr.
+// reflectors stored by cta_pivqr, applied to the identity from the last one
+// back.  H_r changes only rows and columns r.. of the product, so reflector
+// r is the (m - r) x (m - r) update Q[r:, r:] -= 2 v (v^T Q[r:, r:]).  Its
+// dot products are split into P = NT / (m - r) row chunks per column (the
+// partials are added in chunk order), so that each thread's chain of
+// dependent FP64 operations is short; the update spreads the entries over
+// all threads.  All threads of the CTA call it.
 template <int NT>
 __device__ void cta_form_q(double* Q, int ldq, int m, const double* V, int ldv, int k) {
+    __shared__ double fq[2 * NT];
     for (int e = threadIdx.x; e < m * m; e += NT) {
         int i = e / m, j = e % m;
         Q[(size_t)i * ldq + j] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
     for (int r = k - 1; r >= 0; --r) {
-        // Q[r:, :] -= 2 v (v^T Q[r:, :])
-        for (int j = threadIdx.x; j < m; j += NT) {
+        const int c = m - r;     // columns and rows r.. of the update
+        const double* v = V + (size_t)r * ldv + r;   // v_i = v[(i - r) * ldv]
+        if (c > 2 * NT) {
+            for (int j = r + threadIdx.x; j < m; j += NT) {
+                double w = 0.0;
+                for (int i = r; i < m; ++i) w += V[(size_t)i * ldv + r] * Q[(size_t)i * ldq + j];
+                w *= 2.0;
+                if (w != 0.0)
+                    for (int i = r; i < m; ++i) Q[(size_t)i * ldq + j] -= w * V[(size_t)i * ldv + r];
+            }
+            __syncthreads();
+            continue;
+        }
+        const int P = c <= NT ? NT / c : 1;
+        const int len = (c + P - 1) / P;
+        double* wv = P > 1 ? fq + NT : fq;         // 2 v^T Q[r:, j], j = r + jj
+        for (int t = threadIdx.x; t < P * c; t += NT) {
+            const int jj = t % c, ch = t / c;
+            const int i0 = ch * len, i1 = min(c, i0 + len);
             double w = 0.0;
-            for (int i = r; i < m; ++i) w += V[(size_t)i * ldv + r] * Q[(size_t)i * ldq + j];
-            w *= 2.0;
-            if (w != 0.0)
-                for (int i = r; i < m; ++i) Q[(size_t)i * ldq + j] -= w * V[(size_t)i * ldv + r];
+            for (int ii = i0; ii < i1; ++ii) w += v[(size_t)ii * ldv] * Q[(size_t)(r + ii) * ldq + r + jj];
+            if (P > 1) fq[ch * c + jj] = w;
+            else wv[jj] = 2.0 * w;
+        }
+        __syncthreads();
+        if (P > 1) {
+            for (int jj = threadIdx.x; jj < c; jj += NT) {
+                double w = 0.0;
+                for (int ch = 0; ch < P; ++ch) w += fq[ch * c + jj];
+                wv[jj] = 2.0 * w;
+            }
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < c * c; e += NT) {
+            const int ii = e / c, jj = e % c;
+            Q[(size_t)(r + ii) * ldq + r + jj] -= wv[jj] * v[(size_t)ii * ldv];
         }
         __syncthreads();
     }
