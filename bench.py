@@ -491,7 +491,7 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
     ginfo = Mx.h2_info()
     precision = {"mode": "fp32 products, fp64 storage/pivots/counts; every count certified: mixed "
                          "factorizations at mu -/+ Delta (Delta = 64 2^-24 ||A||_inf), FP64 re-run of the "
-                         "shifts whose pair disagrees or whose min |pivot| < 1e-4 ||A||_inf, all inside the "
+                         "shifts whose pair disagrees or whose min |pivot| < 1e-3 ||A||_inf, all inside the "
                          "timed region",
                  "value": world * args.steps * lanes / (ms_mix / 1e3), "unit": "shifts/s",
                  "counts_equal_to_fp64": bool(torch.equal(d_cnt, cnt_fp64)),

@@ -95,7 +95,11 @@ typedef struct {
                             (without hbm_budget) */
     double pivot_guard;  /* mixed precision: a shift whose min |pivot| is below
                             pivot_guard * ||A||_inf is re-run in FP64 (on top
-                            of the certificate of h2_inertia); 0 = 1e-4 */
+                            of the certificate of h2_inertia); 0 = 1e-3.  At
+                            a shift where the reduced blocks are nearly
+                            singular, the FP32 error can exceed Delta; the
+                            mixed pivots there were measured below
+                            4e-4 ||A||_inf */
     void* stream;        /* cudaStream_t for all work of the handle; NULL = a
                             stream created by the library */
     int graphs;          /* 1 (default): each batch replays a CUDA graph

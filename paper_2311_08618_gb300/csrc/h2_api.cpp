@@ -40,7 +40,7 @@ void h2_default_options(h2_options* opt) {
     opt->sketch_cols = 0;
     opt->seed = 0x5EEDull;
     opt->max_lanes = 64;
-    opt->pivot_guard = 1e-4;
+    opt->pivot_guard = 1e-3;
     opt->stream = nullptr;
     opt->graphs = 1;
     opt->tc_schur = 0;
@@ -63,7 +63,7 @@ int h2_build(const double* points, int64_t n, int d, h2_kernel kernel, int leaf,
     if (opt) o = *opt;
     if (o.max_lanes > 65535) { set_error("h2_build: max_lanes above 65535"); return H2_ERR_INVALID_ARG; }
     if (o.max_lanes <= 0) o.max_lanes = o.hbm_budget > 0 ? 65535 : 64;
-    if (!(o.pivot_guard > 0.0)) o.pivot_guard = 1e-4;
+    if (!(o.pivot_guard > 0.0)) o.pivot_guard = 1e-3;
     if (!(o.eps_h2 >= 0.0) || o.fill_cap < 0 || o.sketch_cols < 0 ||
         (o.precision != H2_PREC_FP64 && o.precision != H2_PREC_MIXED && o.precision != H2_PREC_FP64_TC) ||
         (o.admissibility != H2_ADM_BOX && o.admissibility != H2_ADM_CENTER && o.admissibility != H2_ADM_WEAK)) {

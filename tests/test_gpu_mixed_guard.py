@@ -64,6 +64,25 @@ def test_raw_mixed_flips_are_caught(pkg, c1):
     M.close()
 
 
+def test_shift_where_the_fp32_error_exceeds_delta(pkg):
+    """At this shift of the n = 1024 workload (0.0086 above an eigenvalue of
+    A~), the mixed factorization at mu + Delta is wrong by one while the one at
+    mu - Delta is right, so the two agree on the wrong count: the FP32 error
+    there exceeds Delta.  Its smaller mixed min |pivot| is 3.9e-4 ||A||_inf,
+    under the default pivot_guard of 1e-3, so the shift goes to FP64 (with the
+    the benchmark spec's 1e-4 it was certified wrong)."""
+    X = W.uniform_cube(1024, 2, 1)
+    mu = 1184.4096755702722
+    F = pkg.H2Matrix(X, W.LAPLACE_EPS, KP, leaf=64, rank=16, max_lanes=4)
+    want, _ = F.h2_inertia(np.array([mu]))
+    F.close()
+    M = pkg.H2Matrix(X, W.LAPLACE_EPS, KP, leaf=64, rank=16, max_lanes=4, precision=pkg.H2_PREC_MIXED)
+    got, _ = M.h2_inertia(np.array([mu]))
+    assert M.h2_info()["guard_reruns"] == 1
+    M.close()
+    assert got[0] == want[0]
+
+
 def test_device_entry_point_is_certified(pkg, c1):
     import torch
     X, shifts, want = c1
