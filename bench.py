@@ -857,7 +857,7 @@ def _serving_run(args, rate, seconds, seed, mats=None, lanes=None, grace_s=25.0)
     t0 = time.perf_counter()
     done, unfinished = serving.run_open_loop(srv, arr, seconds, deadline_s=seconds + grace_s)
     wall = time.perf_counter() - t0
-    res = {"arrivals": "Poisson %.0f q/s for %.0f s" % (rate, seconds), "offered": len(arr),
+    res = {"arrivals": "Poisson %g q/s for %g s" % (rate, seconds), "offered": len(arr),
            "completed": len(done), "unfinished": unfinished, "wall_s": wall,
            "eigs_per_s": len(done) / wall, "shifts_per_s": srv.shifts_evaluated / wall, "ticks": srv.ticks,
            "ms_per_tick": 1e3 * srv.host_s / max(1, srv.ticks),
