@@ -141,6 +141,12 @@ typedef struct {
                             scratch); 0 (default): one stream, colour after
                             colour, which measured faster (the concurrent
                             Schur blocks slow the solves on the critical path) */
+    int shifts_per_interval; /* h2_kth_eig rounds: at most this many shifts per
+                            bracket still wider than tol (default 16), so
+                            that few brackets do not take every lane: at
+                            n = 1024 one k converges faster with 16 shifts
+                            per round (17-section) than with 64; 0 = every
+                            round uses all max_lanes lanes */
 } h2_options;
 
 /* Fills *opt with the defaults above.  Never fails. */

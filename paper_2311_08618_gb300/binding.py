@@ -34,7 +34,8 @@ class Options(C.Structure):
                 ("fill_cap", C.c_int), ("sketch_cols", C.c_int), ("seed", C.c_uint64),
                 ("max_lanes", C.c_int), ("pivot_guard", C.c_double), ("stream", C.c_void_p),
                 ("graphs", C.c_int), ("recomp_cluster_cols", C.c_int), ("autotune", C.c_int),
-                ("hbm_budget", C.c_size_t), ("tc_schur", C.c_int), ("lookahead", C.c_int)]
+                ("hbm_budget", C.c_size_t), ("tc_schur", C.c_int), ("lookahead", C.c_int),
+                ("shifts_per_interval", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -45,6 +45,7 @@ void h2_default_options(h2_options* opt) {
     opt->graphs = 1;
     opt->tc_schur = 0;
     opt->lookahead = 0;
+    opt->shifts_per_interval = 16;
 }
 
 const char* h2_last_error(void) { return g_last_error.c_str(); }

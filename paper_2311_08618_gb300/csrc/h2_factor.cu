@@ -2459,6 +2459,7 @@ struct KthLoop {
     int rounds;                 // rounds with work in this launch
     unsigned long long shifts;  // shifts evaluated in this launch
     int stopped;                // 1: the round cap ended the loop
+    int per_interval;           // shifts per interval and round (0: all lanes)
 };
 
 struct FactorState {
@@ -3712,9 +3713,12 @@ int run_inertia_host(h2_matrix* h, const double* shifts, int64_t ns, int64_t* co
 // missed duplicate would only repeat work).  One CTA scans the brackets in
 // chunks (block prefix sums), keeps the first `lanes` distinct intervals
 // wider than tol in k order and spreads the lanes over them: interval u gets
-// q or q + 1 equally spaced interior points.
+// q or q + 1 equally spaced interior points.  per > 0 caps the round at per
+// shifts per interval: with few intervals, a round of fewer lanes is cheaper
+// by more than the fewer bits of narrowing it gives (one k at n = 1024: 16
+// shifts per round beat 64).
 __device__ __forceinline__ void bisect_plan_body(const double* lo, const double* hi, int nk, double tol, int lanes,
-                                                 double* shifts, int* active, int* nact, int* first) {
+                                                 int per, double* shifts, int* active, int* nact, int* first) {
     __shared__ int wsum[32];
     __shared__ int s_base;
     const int t = threadIdx.x, w = t >> 5, l = t & 31, nw = (blockDim.x + 31) >> 5;
@@ -3747,13 +3751,14 @@ __device__ __forceinline__ void bisect_plan_body(const double* lo, const double*
         __syncthreads();
     }
     const int nd = s_base;
+    const int use = (per > 0 && nd > 0) ? (int)min((long long)lanes, (long long)nd * per) : lanes;
     if (t == 0) {
         *nact = nd;
-        *active = nd > 0 ? lanes : 0;
+        *active = nd > 0 ? use : 0;
     }
-    const int m = min(nd, lanes);
+    const int m = min(nd, use);
     if (m == 0) return;
-    const int q = lanes / m, extra = lanes % m;
+    const int q = use / m, extra = use % m;
     for (int u = t; u < m; u += blockDim.x) {
         const int qu = q + (u < extra ? 1 : 0);
         const int off = u * q + min(u, extra);
@@ -3764,9 +3769,9 @@ __device__ __forceinline__ void bisect_plan_body(const double* lo, const double*
 }
 
 __global__ void __launch_bounds__(1024) k_bisect_plan(const double* lo, const double* hi, int nk, double tol,
-                                                      int lanes, double* shifts, int* active, int* nact,
+                                                      int lanes, int per, double* shifts, int* active, int* nact,
                                                       int* first) {
-    bisect_plan_body(lo, hi, nk, tol, lanes, shifts, active, nact, first);
+    bisect_plan_body(lo, hi, nk, tol, lanes, per, shifts, active, nact, first);
 }
 
 
@@ -3777,13 +3782,13 @@ __global__ void __launch_bounds__(1024) k_bisect_plan_loop(const double* lo, con
                                                            int lanes, double* shifts, int* active, int* nact,
                                                            int* first, cudaGraphConditionalHandle cond) {
     const int nk = par->nk;
-    bisect_plan_body(lo, hi, nk, par->width, lanes, shifts, active, nact, first);
+    bisect_plan_body(lo, hi, nk, par->width, lanes, par->per_interval, shifts, active, nact, first);
     if (threadIdx.x == 0) {
         const int nd = *nact;
         int go = nd > 0 ? 1 : 0;
         if (go) {
             par->rounds += 1;
-            par->shifts += (unsigned long long)lanes;
+            par->shifts += (unsigned long long)*active;
             if (par->rounds >= par->max_rounds) {
                 par->stopped = 1;
                 go = 0;
@@ -3839,8 +3844,8 @@ static int kth_round(h2_matrix* h, int nk, double width, int mixed, int* nact) {
     Workspace& ws = h->ws;
     FactorState* fs = state_of(h);
     cudaStream_t st = h->stream;
-    k_bisect_plan<<<1, 1024, 0, st>>>(fs->d_lo, fs->d_hi, nk, width, ws.lanes, ws.d_shifts, fs->d_active, fs->d_nact,
-                                      fs->d_first);
+    k_bisect_plan<<<1, 1024, 0, st>>>(fs->d_lo, fs->d_hi, nk, width, ws.lanes, h->opt.shifts_per_interval,
+                                      ws.d_shifts, fs->d_active, fs->d_nact, fs->d_first);
     int used = 0;
     CK(cudaMemcpyAsync(nact, fs->d_nact, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&used, fs->d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -3903,7 +3908,7 @@ static int run_loop(h2_matrix* h, int nk, double width, int mixed, int* rounds) 
     }
     int rc;
     if (!fs->loop_exec[mixed] && (rc = build_loop_graph(h, mixed))) return rc;
-    KthLoop par{nk, width, 4096, 0, 0ull, 0};
+    KthLoop par{nk, width, 4096, 0, 0ull, 0, h->opt.shifts_per_interval};
     CK(cudaMemcpyAsync(fs->d_loop, &par, sizeof(par), cudaMemcpyHostToDevice, st));
     CK(cudaGraphLaunch(fs->loop_exec[mixed], st));
     CK(cudaMemcpyAsync(&par, fs->d_loop, sizeof(par), cudaMemcpyDeviceToHost, st));

@@ -48,11 +48,12 @@ def test_struct_layouts_match_header(pkg, tmp_path):
 #include <stddef.h>
 #include "h2eig.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(h2_options), offsetof(h2_options, stream),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(h2_options), offsetof(h2_options, stream),
          offsetof(h2_options, max_lanes), sizeof(h2_stats), offsetof(h2_stats, lanes),
          sizeof(h2_kernel), offsetof(h2_options, hbm_budget), offsetof(h2_stats, cap_bound),
          offsetof(h2_stats, max_residual), sizeof(h2_export_buf), offsetof(h2_export_buf, offsets),
-         offsetof(h2_export_buf, B), offsetof(h2_options, tc_schur), offsetof(h2_options, lookahead));
+         offsetof(h2_export_buf, B), offsetof(h2_options, tc_schur), offsetof(h2_options, lookahead),
+         offsetof(h2_options, shifts_per_interval));
   return 0;
 }
 """)
@@ -64,7 +65,7 @@ int main(void) {
             C.sizeof(b.Stats), b.Stats.lanes.offset, C.sizeof(b.Kernel), b.Options.hbm_budget.offset,
             b.Stats.cap_bound.offset, b.Stats.max_residual.offset, C.sizeof(b.ExportBuf),
             b.ExportBuf.offsets.offset, b.ExportBuf.B.offset, b.Options.tc_schur.offset,
-            b.Options.lookahead.offset]
+            b.Options.lookahead.offset, b.Options.shifts_per_interval.offset]
     assert got == want
 
 

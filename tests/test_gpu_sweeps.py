@@ -70,3 +70,30 @@ def test_master_worker_on_replicas(pkg, circle):
     assert e.value.code == -5
     for M in reps:
         M.close()
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_shifts_per_interval_cap(pkg, prec):
+    """The round cap of h2_kth_eig (at most shifts_per_interval shifts per
+    unfinished bracket): a few k on a 64-lane handle converge to the same
+    eigenvalues within tol as with every lane per round, using at most
+    16 shifts per bracket and round."""
+    X = W.uniform_cube(1024, 2, 1)
+    ev = dense.eigenvalues(dense.kernel_matrix(W.LAPLACE_EPS, KP, X))
+    ks = [1, 512, 700]
+    tol = 1e-8
+    out = {}
+    for per in (16, 0):
+        M = pkg.H2Matrix(X, W.LAPLACE_EPS, KP, leaf=64, rank=16, max_lanes=64,
+                         precision=getattr(pkg, "H2_PREC_" + prec), shifts_per_interval=per)
+        lam, eb = M.h2_kth_eig(ks, tol)
+        info = M.h2_info()
+        out[per] = (lam, info)
+        M.close()
+        assert np.all(np.abs(lam - ev[np.array(ks) - 1]) <= tol / 2 + 1e-8 * np.abs(ev).max())
+    lam16, info16 = out[16]
+    lam0, info0 = out[0]
+    assert np.all(np.abs(lam16 - lam0) <= tol)
+    if prec == "FP64":
+        assert info16["last_shifts"] <= 16 * len(ks) * info16["last_rounds"]
+        assert info16["last_shifts"] < info0["last_shifts"]
