@@ -601,7 +601,8 @@ def _ours_on_stream(args, rank, world, local, dist, pkg, dev, stream):
         line["cpu_baseline"] = {"value": rate, "unit": "shifts/s", "cores": cores, "kind": "oracle",
                                 "sample": "%d shifts of step 1 (%.1f s wall, about %.0f s of CPU work, "
                                           "one process per core)" % (len(sample), secs, secs * cores),
-                                "counts_equal_to_gpu": "%d/%d" % (agree, len(sample))}
+                                "counts_equal_to_gpu": "%d/%d" % (agree, len(sample)),
+                                "seconds_per_shift_one_core": secs * cores / max(1, len(sample))}
     if rank == 0:
         print(json.dumps(line), flush=True)
     M.close()

@@ -486,8 +486,8 @@ int h2_export(h2_handle h, h2_export_buf* buf);
  * `iters` steps of power iteration from one seeded start vector.  A~ x is the
  * nested H^2 product (skeleton coordinates up through the transfer matrices,
  * couplings, back down, plus the dense near blocks; Sec. 3.1), A x evaluates
- * the kernel entries on the fly (O(n^2) per step).  North-star criterion:
- * err2 / norm2 <= 1e-8.  Power iteration approaches both norms from below.
+ * the kernel entries on the fly (O(n^2) per step).  The accuracy requirement
+ * of the compression is err2 / norm2 <= 1e-8.  Power iteration approaches both norms from below.
  * Blocks until done.  Errors: H2_ERR_INVALID_ARG (iters < 1, null pointers),
  * H2_ERR_OOM, H2_ERR_CUDA.
  */

@@ -2333,7 +2333,7 @@ __global__ void k_finish(const unsigned long long* neg, const unsigned long long
 // the mixed counts at mu - Delta and mu + Delta agree (= c), then nu is
 // constant on [mu - Delta + ||E||, mu + Delta - ||E||], an interval around
 // mu, so nu(mu) = c.  Shifts whose pair disagrees, or whose min |pivot| is
-// below the benchmark spec's threshold, are factorized again in FP64.
+// below pivot_guard * ||A||_inf, are factorized again in FP64.
 
 // lanes 2i and 2i + 1 of the next mixed batch: mu_i - Delta and mu_i + Delta
 __global__ void k_guard_pairs(const double* req, int nc, double delta, double* shifts, int* active) {

@@ -1,6 +1,6 @@
 """GPU compression error and the exported representation (Sec. 3.1).
 
-North-star criterion: ||A - A~||_2 / ||A||_2 <= 1e-8 for the GPU's own A~.
+Accuracy requirement of the compression: ||A - A~||_2 / ||A||_2 <= 1e-8 for the GPU's own A~.
 The GPU representation is exported (h2_export) and written out densely here;
 its error is measured three ways: from that dense A~ on the host, by the
 library's device power iteration (h2_compression_error), and against the

@@ -1,5 +1,5 @@
 """The certified mixed-precision counts (Sec. 4.1, Parlett's criterion, and
-the benchmark spec's FP64 re-run rule) on every entry point that returns counts:
+the FP64 re-run of small-pivot shifts) on every entry point that returns counts:
 h2_inertia, h2_inertia_device, group batches, and the serving and batching
 layers above them.
 
@@ -70,7 +70,7 @@ def test_shift_where_the_fp32_error_exceeds_delta(pkg):
     mu - Delta is right, so the two agree on the wrong count: the FP32 error
     there exceeds Delta.  Its smaller mixed min |pivot| is 3.9e-4 ||A||_inf,
     under the default pivot_guard of 1e-3, so the shift goes to FP64 (with the
-    the benchmark spec's 1e-4 it was certified wrong)."""
+    guard at 1e-4 it was certified wrong)."""
     X = W.uniform_cube(1024, 2, 1)
     mu = 1184.4096755702722
     F = pkg.H2Matrix(X, W.LAPLACE_EPS, KP, leaf=64, rank=16, max_lanes=4)
