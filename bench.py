@@ -61,10 +61,10 @@ def _points(wl):
         return W.cylinder_lattice(wl["n"], wl["seed"])
     return W.uniform_cube(wl["n"], wl["d"], wl["seed"])
 METRIC = "LDL-inertia shifts/sec (FP64); k-th eigs/sec at tol 1e-8 with p50/p99"
-FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 (profiling recipe table); not in MEASURED_PEAKS
+FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 rate (the measured-peaks file has no FP64 entry)
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per k_schur launch,
-# the mean over the 31 launches of one batch, from the ncu capture summarised in
-# profiles/k_schur_laplace2d_n1024_256lanes.md; valid for that workload and lane
+# the mean over the 31 launches of one batch, from the committed ncu summary of
+# k_schur at this workload under profiles/; valid for that workload and lane
 # count while the kernel's source is unchanged (sha256 prefix of its text)
 NCU_TRAFFIC = {"kernel": "k_schur", "workload": "laplace2d_n1024", "lanes": 256,
                "bytes_per_launch": 323.52e6, "source_sha": "7ddfe31f5f9903ac"}
