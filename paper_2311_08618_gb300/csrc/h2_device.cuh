@@ -138,6 +138,45 @@ __device__ __forceinline__ double block_sum1(double v, double* buf, int par) {
     return r;
 }
 
+// Ordering key of |x|: the bit pattern of a non-negative double, read as an
+// unsigned integer, orders like its value (a NaN ranks above +inf).  Pivot
+// searches compare these keys in the integer pipes.
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// Block argmax of (key, index): the largest key, the smallest index on ties,
+// the same on every thread.  Within a warp three integer reductions (high
+// word, low word among the maxima, index among the exact maxima); across
+// warps one barrier and a scan of the warps' winners.  bk / bi: 2 * NTH / 32
+// entries each, double-buffered by par like block_argmax1.
+template <int NTH>
+__device__ __forceinline__ int block_argmax_key(unsigned long long key, int idx, unsigned long long* bk, int* bi,
+                                                int par, unsigned long long* out_key) {
+    constexpr int NW = NTH / 32;
+    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    const unsigned mi = __reduce_min_sync(0xffffffffu, (hi == mh && lo == ml) ? (unsigned)idx : 0xffffffffu);
+    unsigned long long* k2 = bk + par * NW;
+    int* i2 = bi + par * NW;
+    if ((threadIdx.x & 31) == 0) {
+        k2[threadIdx.x >> 5] = ((unsigned long long)mh << 32) | ml;
+        i2[threadIdx.x >> 5] = (int)min(mi, 0x7fffffffu);
+    }
+    __syncthreads();
+    unsigned long long kb = k2[0];
+    int ib = i2[0];
+#pragma unroll
+    for (int u = 1; u < NW; ++u) {
+        const unsigned long long ku = k2[u];
+        const int iu = i2[u];
+        if (ku > kb || (ku == kb && iu < ib)) { kb = ku; ib = iu; }
+    }
+    *out_key = kb;
+    return ib;
+}
+
 // ------------------------------------------------- pivoted Householder QR --
 // Householder QR with column pivoting of Y (m x s, row-major, leading
 // dimension ldy), in place, stopped when the Frobenius norm of the
@@ -176,9 +215,13 @@ __device__ int cta_pivqr(double* Y, int ldy, int m, int s, double tol, int cap, 
             if (bad && threadIdx.x == 0) *bad = 1;
             break;
         }
-        if (sqrt(total) <= tol) break;
-        double bv;
-        int jp = block_argmax1<NT>(best, bi, red, redi, par, &bv);
+        if (total <= tol * tol) break;
+        // pivot: the largest norm (integer keys of the non-negative norms,
+        // smallest index on ties), no FP64 compare on the step's chain
+        unsigned long long bk;
+        const bool has = bi != 0x7fffffff;
+        int jp = block_argmax_key<NT>(has ? abs_key(best) : 0ull, has ? bi : 0x7fffffff,
+                                      reinterpret_cast<unsigned long long*>(red), redi, par, &bk);
         par ^= 1;
         if (jp < k || jp >= s) jp = k;
         if (jp != k)
@@ -199,19 +242,14 @@ __device__ int cta_pivqr(double* Y, int ldy, int m, int s, double tol, int cap, 
         double nx = sqrt(nx2);
         double x0 = Y[(size_t)k * ldy + k];
         double alpha = x0 >= 0.0 ? -nx : nx;
-        // |v|^2 = |x|^2 - 2 alpha x0 + alpha^2
+        // |v|^2 = |x|^2 - 2 alpha x0 + alpha^2 = 2 |x|^2 + 2 |x0| |x| (alpha has
+        // the opposite sign of x0, so nothing cancels): no second reduction
         double v0 = x0 - alpha;
-        double nv2 = 0.0;
-        for (int i = k + threadIdx.x; i < m; i += NT) {
-            double x = (i == k) ? v0 : Y[(size_t)i * ldy + k];
-            nv2 += x * x;
-        }
-        nv2 = block_sum1<NT>(nv2, red, par);
-        par ^= 1;
-        double nv = sqrt(nv2);
+        double nv = sqrt(2.0 * nx2 + 2.0 * fabs(x0) * nx);
+        const double inv_nv = nv > 0.0 ? 1.0 / nv : 0.0;
         for (int i = threadIdx.x; i < m; i += NT) {
             double x = 0.0;
-            if (i >= k && nv > 0.0) x = ((i == k) ? v0 : Y[(size_t)i * ldy + k]) / nv;
+            if (i >= k && nv > 0.0) x = ((i == k) ? v0 : Y[(size_t)i * ldy + k]) * inv_nv;
             V[(size_t)i * ldv + k] = x;
         }
         __syncthreads();
@@ -466,45 +504,6 @@ __device__ void cta_bk_ldl(double* S, int lds, int n, int* perm, int* piv, doubl
         *minpiv = fmin(*minpiv, mp);
     }
     __syncthreads();
-}
-
-// Ordering key of |x|: the bit pattern of a non-negative double, read as an
-// unsigned integer, orders like its value (a NaN ranks above +inf).  Pivot
-// searches compare these keys in the integer pipes.
-__device__ __forceinline__ unsigned long long abs_key(double x) {
-    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
-}
-
-// Block argmax of (key, index): the largest key, the smallest index on ties,
-// the same on every thread.  Within a warp three integer reductions (high
-// word, low word among the maxima, index among the exact maxima); across
-// warps one barrier and a scan of the warps' winners.  bk / bi: 2 * NTH / 32
-// entries each, double-buffered by par like block_argmax1.
-template <int NTH>
-__device__ __forceinline__ int block_argmax_key(unsigned long long key, int idx, unsigned long long* bk, int* bi,
-                                                int par, unsigned long long* out_key) {
-    constexpr int NW = NTH / 32;
-    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
-    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
-    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
-    const unsigned mi = __reduce_min_sync(0xffffffffu, (hi == mh && lo == ml) ? (unsigned)idx : 0xffffffffu);
-    unsigned long long* k2 = bk + par * NW;
-    int* i2 = bi + par * NW;
-    if ((threadIdx.x & 31) == 0) {
-        k2[threadIdx.x >> 5] = ((unsigned long long)mh << 32) | ml;
-        i2[threadIdx.x >> 5] = (int)min(mi, 0x7fffffffu);
-    }
-    __syncthreads();
-    unsigned long long kb = k2[0];
-    int ib = i2[0];
-#pragma unroll
-    for (int u = 1; u < NW; ++u) {
-        const unsigned long long ku = k2[u];
-        const int iu = i2[u];
-        if (ku > kb || (ku == kb && iu < ib)) { kb = ku; ib = iu; }
-    }
-    *out_key = kb;
-    return ib;
 }
 
 // S[i][j] -= a_i b_j (+ a2_i b2_j) over the lower triangle o <= j <= i < n of

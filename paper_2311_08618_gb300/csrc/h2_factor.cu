@@ -502,7 +502,7 @@ __device__ int cluster_pivqr(cg::cluster_group& cl, int g, double* Y, int ldy, i
             if (bad && threadIdx.x == 0 && g == 0) *bad = 1;
             break;
         }
-        if (sqrt(total) <= tol) break;
+        if (total <= tol * tol) break;
         if (jp < k || jp >= s) jp = k;
         if (g == 0 && jp != k)
             for (int i = threadIdx.x; i < m; i += NT) {
@@ -523,17 +523,12 @@ __device__ int cluster_pivqr(cg::cluster_group& cl, int g, double* Y, int ldy, i
         const double x0 = Y[(size_t)k * ldy + k];
         const double alpha = x0 >= 0.0 ? -nx : nx;
         const double v0 = x0 - alpha;
-        double nv2 = 0.0;
-        for (int i = k + threadIdx.x; i < m; i += NT) {
-            double x = (i == k) ? v0 : Y[(size_t)i * ldy + k];
-            nv2 += x * x;
-        }
-        nv2 = block_sum1<NT>(nv2, red, par);
-        par ^= 1;
-        const double nv = sqrt(nv2);
+        // |v|^2 = 2 |x|^2 + 2 |x0| |x|, as in cta_pivqr
+        const double nv = sqrt(2.0 * nx2 + 2.0 * fabs(x0) * nx);
+        const double inv_nv = nv > 0.0 ? 1.0 / nv : 0.0;
         for (int i = threadIdx.x; i < m; i += NT) {
             double x = 0.0;
-            if (i >= k && nv > 0.0) x = ((i == k) ? v0 : Y[(size_t)i * ldy + k]) / nv;
+            if (i >= k && nv > 0.0) x = ((i == k) ? v0 : Y[(size_t)i * ldy + k]) * inv_nv;
             sv[i] = x;
             if (g == 0) V[(size_t)i * ldv + k] = x;
         }
