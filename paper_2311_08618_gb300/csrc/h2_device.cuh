@@ -231,14 +231,9 @@ __device__ int cta_pivqr(double* Y, int ldy, int m, int s, double tol, int cap, 
                 Y[(size_t)i * ldy + jp] = t;
             }
         __syncthreads();
-        // reflector from x = Y[k:, k]
-        double nx2 = 0.0;
-        for (int i = k + threadIdx.x; i < m; i += NT) {
-            double x = Y[(size_t)i * ldy + k];
-            nx2 += x * x;
-        }
-        nx2 = block_sum1<NT>(nx2, red, par);
-        par ^= 1;
+        // reflector from x = Y[k:, k]; |x|^2 is the pivot column's norm that
+        // won the search (summed over rows k.. in the previous update)
+        const double nx2 = __longlong_as_double((long long)bk);
         double nx = sqrt(nx2);
         double x0 = Y[(size_t)k * ldy + k];
         double alpha = x0 >= 0.0 ? -nx : nx;

@@ -511,14 +511,9 @@ __device__ int cluster_pivqr(cg::cluster_group& cl, int g, double* Y, int ldy, i
                 Y[(size_t)i * ldy + jp] = t;
             }
         cl.sync();
-        // reflector from x = Y[k:, k], identical on every CTA
-        double nx2 = 0.0;
-        for (int i = k + threadIdx.x; i < m; i += NT) {
-            double x = Y[(size_t)i * ldy + k];
-            nx2 += x * x;
-        }
-        nx2 = block_sum1<NT>(nx2, red, par);
-        par ^= 1;
+        // reflector from x = Y[k:, k], identical on every CTA; |x|^2 is the
+        // winning column norm of the search
+        const double nx2 = bv;
         const double nx = sqrt(nx2);
         const double x0 = Y[(size_t)k * ldy + k];
         const double alpha = x0 >= 0.0 ? -nx : nx;
