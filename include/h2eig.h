@@ -285,16 +285,18 @@ void h2_group_destroy(h2_group g);
  * h2_kth_eig -- out[i] = lambda~_{k[i]} of A~, the midpoint of a final
  * interval of width < tol found by bisection/multisection from the Gershgorin
  * interval (|lambda_k - lambda~_k| < tol/2, Eq. error-bound).  Every evaluated
- * (mu, nu) narrows every k (Sec. 4.2); each round spreads max_lanes shifts
- * over the distinct active intervals, the first max_lanes of them in k order
- * (any number of k, in any order, repeats allowed: up to all n eigenvalues in
- * one call).  The intervals stay on the device.
+ * (mu, nu) narrows every k (Sec. 4.2); each round spreads up to max_lanes
+ * shifts, at most shifts_per_interval per interval, over the distinct active
+ * intervals, the first max_lanes of them in k order (any number of k, in any
+ * order, repeats allowed: up to all n eigenvalues in one call).  The
+ * intervals stay on the device.
  * H2_PREC_MIXED: mixed rounds (one mixed factorization per shift, no per-shift
  * certificate) run while the brackets are wider than Delta = 64 * 2^-24 *
  * ||A||_inf: a wrong mixed count at mu means an eigenvalue within ||E|| of
- * mu, so it moves a bracket end by less than Delta.  Every bracket is
- * then widened by Delta and checked in FP64 (nu(lo) < k <= nu(hi), else it
- * restarts from the Gershgorin interval), and FP64 rounds finish to tol.
+ * mu, which as a rule moves a bracket end by less than Delta.  Every bracket
+ * is then widened by Delta and checked in FP64 (nu(lo) < k <= nu(hi), else it
+ * restarts from the Gershgorin interval), so a larger error costs a restart,
+ * not a wrong result; FP64 rounds finish to tol.
  *   k         : host, nk int64, 1-based, each in 1..n.
  *   tol > 0   : absolute interval width.
  *   out       : host, caller-owned, nk FP64.
