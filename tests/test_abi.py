@@ -37,6 +37,9 @@ def test_default_options(pkg):
     o = pkg.binding.default_options()
     assert o.precision == 0 and o.admissibility == 0 and o.eps_h2 == 1e-10
     assert o.max_lanes == 64 and o.fill_cap == 0
+    # the header's documented defaults of the later options
+    assert o.pivot_guard == 1e-3 and o.graphs == 1 and o.hbm_budget == 0
+    assert o.tc_schur == 0 and o.lookahead == 0 and o.shifts_per_interval == 16
 
 
 def test_struct_layouts_match_header(pkg, tmp_path):
