@@ -53,3 +53,36 @@ def test_planner_rejects_bad_arguments(binding):
         binding.plan_summary(W.uniform_cube(10, 2, 1), 1)          # leaf < 2
     with pytest.raises(binding.H2Error):
         binding.plan_summary(W.uniform_cube(10, 2, 1), 4, rule=7)  # unknown rule
+
+
+@pytest.mark.parametrize("name,mk,leaf,rule", CASES[:8], ids=[c[0] for c in CASES[:8]])
+def test_colour_writes_are_disjoint(binding, name, mk, leaf, rule):
+    """What the concurrent launches of one colour and the lookahead schedule
+    rely on, checked on the planner's colours: within a colour no two clusters
+    share a stored block (near or fill), and no Schur target block (x, y),
+    x, y in {p} + near(p), belongs to two clusters, so every block takes at
+    most one Schur update per colour."""
+    X = mk()
+    _, _, colours = binding.plan_summary(X, leaf, 1.0, rule)
+    st = oh2.build_structure(X, leaf, 1.0, rule)
+    for l in range(st.L + 1):
+        near = np.asarray(st.near[l]).astype(bool)
+        fill = np.asarray(st.fill[l]).astype(bool)
+        col = np.asarray(colours[l])
+        nc = len(col)
+        for c in range(col.max() + 1):
+            members = np.nonzero(col == c)[0]
+            written = {}
+            rows = {}
+            for p in members:
+                tg = [p] + [x for x in range(nc) if x != p and near[p, x]]
+                for i, a in enumerate(tg):
+                    for b in tg[:i + 1]:
+                        key = (max(a, b), min(a, b))
+                        assert key not in written, (l, c, p, written.get(key), key)
+                        written[key] = p
+                rows[p] = {x for x in range(nc) if x != p and (near[p, x] or fill[p, x])}
+            for p in members:
+                for q in members:
+                    if p != q:
+                        assert q not in rows[p], (l, c, p, q)
